@@ -1,0 +1,177 @@
+/*
+ * pasm.h -- C ABI of the GB300 (sm_103a) parallel augmented subspace method.
+ *
+ * The library computes the k smallest eigenpairs of the generalized finite
+ * element eigenproblem A u = lambda M u (Section 2: the discrete problem on the
+ * linear element space V_h) with the parallel augmented subspace method of
+ * Xu, Xie and Zhang: Algorithm 1 (one correction step) applied to all k pairs
+ * at once, inside Algorithm 2 (the parallel scheme).  The k pairs never
+ * exchange data (Section 3.2: the correction runs independently per pair and
+ * needs no orthogonalisation), so the library batches them: every block vector
+ * is an n x k row-major array and every sparse product reuses each matrix entry
+ * k times.
+ *
+ * Conventions shared by all entry points
+ *   - Level 0 is the coarse space V_H; level n_levels-1 is the finest V_h.
+ *     P[l] is the interpolation from level l to level l+1 (n_{l+1} x n_l), so
+ *     the nested spaces of Section 3.1 are given by their prolongations.
+ *   - CSR arrays are HOST pointers owned by the caller.  The library copies them
+ *     during pasm_setup; the caller may free them afterwards.
+ *   - Block vectors U are n x k, row-major (U[i*k + j] = entry i of pair j),
+ *     float64.  Vector and eigenvalue arguments may be host or device pointers
+ *     (the library detects which; copies run on the context's stream).
+ *   - Eigenvectors are a-normalised, a(u, u) = u^T A u = 1 (the normalisation
+ *     of the weak eigenproblem in Section 2), with the sign fixed by
+ *     b(u_new, u~) > 0 (u~ = the multigrid iterate of the step).
+ *   - Every function returns a pasm_status code (0 = success).  On error no
+ *     output is written unless stated.  pasm_strerror names the code.
+ *   - A context owns all its device memory and its CUDA graph; it is not
+ *     thread-safe; distinct contexts are independent.
+ */
+#ifndef PASM_H
+#define PASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PASM_OK = 0,
+  PASM_EINVAL = 1,      /* malformed CSR, shape mismatch, bad option or size   */
+  PASM_EK_TOO_BIG = 2,  /* k > dim V_H: the coarse space cannot seed k pairs   */
+  PASM_ENOMEM = 3,      /* device or host allocation failed                     */
+  PASM_ECUDA = 4,       /* a CUDA runtime call failed                           */
+  PASM_ENOTCONV = 5,    /* max_steps reached with pairs still active            */
+  PASM_EDEGENERATE = 6, /* bordered mass matrix singular for a pair (u~ in V_H) */
+  PASM_ENAN = 7,        /* a NaN/Inf appeared in a pair                         */
+  PASM_ESTATE = 8,      /* call out of order (e.g. pasm_step before pasm_init)  */
+  PASM_ENOTPD = 9       /* coarse A_H or M_H not symmetric positive definite    */
+} pasm_status;
+
+/* Per-pair status values written by pasm_get / pasm_solve. */
+enum {
+  PASM_PAIR_ACTIVE = 0,     /* still iterating                                 */
+  PASM_PAIR_CONVERGED = 1,  /* |lambda_new - lambda_old| / lambda_new < tol    */
+  PASM_PAIR_DEGENERATE = 2, /* kept its previous pair this step (u~ in V_H)     */
+  PASM_PAIR_NAN = 3         /* frozen after a NaN/Inf                           */
+};
+
+enum { PASM_FP64 = 0, PASM_MIXED = 1 };           /* precision of the V-cycles   */
+enum { PASM_SCORE_A = 0, PASM_SCORE_B = 1 };      /* normalisation in the score  */
+enum { PASM_INIT_COARSE = 0, PASM_INIT_NESTED = 1 };
+
+/* A sparse matrix in CSR form: n_rows x n_cols, nnz entries, 32-bit indices,
+ * float64 values, column indices ascending within each row. */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int64_t nnz;
+  const int32_t* row_ptr; /* n_rows + 1 entries, row_ptr[0] = 0, nondecreasing */
+  const int32_t* col;     /* nnz entries in [0, n_cols)                         */
+  const double* val;      /* nnz entries                                        */
+} pasm_csr;
+
+/* Method parameters.  pasm_default_opts fills the defaults in brackets. */
+typedef struct {
+  double omega;        /* damped Jacobi weight [2/3]                             */
+  int nu_pre;          /* pre-smoothing sweeps per level [2]                     */
+  int nu_post;         /* post-smoothing sweeps per level [2]                    */
+  int cycles_per_step; /* V-cycles per correction step (Algorithm 1 step 1) [2]  */
+  int max_steps;       /* step limit in pasm_solve [100]                         */
+  int precision;       /* PASM_FP64: all arithmetic float64; PASM_MIXED: V-cycles
+                          in float32 as a defect correction under float64
+                          residuals, bordering and small eigensolve [PASM_FP64] */
+  int score_norm;      /* PASM_SCORE_A (a-normalised Ritz vectors, as the paper
+                          states the normalisation) or PASM_SCORE_B [A]          */
+  int init;            /* PASM_INIT_COARSE: prolongated coarse eigenpairs
+                          (Algorithm 2 step 1 on V_H, then step 2(B));
+                          PASM_INIT_NESTED: additionally one correction step on
+                          every intermediate level (Algorithm 2 step 2(A))
+                          [PASM_INIT_COARSE]                                     */
+  int use_graph;       /* capture the finest-level step in a CUDA graph [1]      */
+} pasm_opts;
+
+typedef struct pasm_ctx pasm_ctx;
+
+/* Fill *opts with the defaults listed above. */
+void pasm_default_opts(pasm_opts* opts);
+
+/* Build a context: validate and copy the level hierarchy to the device, form
+ * the float32 shadows used by PASM_MIXED, and compute the coarse generalized
+ * eigendecomposition A_H Q = M_H Q Lambda_H (Q^T M_H Q = I) once (Algorithm 2
+ * step 1 on V_H).
+ *   out       receives the context (NULL on error).
+ *   n_levels  >= 1 levels; A[l], M[l] square n_l x n_l symmetric (the library
+ *             relies on symmetry and does not check it), P[l] n_{l+1} x n_l.
+ *   opts      may be NULL (defaults).
+ *   stream    a cudaStream_t to run on, or NULL for the default stream.
+ * Errors: PASM_EINVAL (shapes/CSR), PASM_ENOTPD (A_H or M_H), PASM_ENOMEM,
+ * PASM_ECUDA. */
+int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* M,
+               const pasm_csr* P, const pasm_opts* opts, void* stream);
+
+/* Set the k pairs to iterate (Algorithm 2).  lambda0 (k) and U0 (n x k) give
+ * an explicit starting state (host or device; both NULL = the start selected
+ * by opts.init).  tol is the per-pair freeze threshold on the relative
+ * eigenvalue change.  Errors: PASM_EK_TOO_BIG (k > dim V_H when starting from
+ * the coarse space), PASM_EINVAL (k < 1 or one of lambda0/U0 NULL). */
+int pasm_init(pasm_ctx* ctx, int k, double tol, const double* lambda0, const double* U0);
+
+/* One correction step (Algorithm 1) for every active pair on the finest
+ * level: k multigrid solves of A u^ = lambda M u started from u, then the
+ * bordered eigenproblem on V_H + span{u~} and the selection of the Ritz pair
+ * with the largest |b(u_{H,h}, u~)|.  Runs asynchronously on the context's
+ * stream; *n_active (may be NULL) receives the number of pairs still active,
+ * which synchronises the stream.  Errors: PASM_ESTATE, PASM_ECUDA. */
+int pasm_step(pasm_ctx* ctx, int* n_active);
+
+/* Copy the current state out: lambda (k), U (n x k), steps (k, correction
+ * steps taken per pair), status (k, PASM_PAIR_*).  Any pointer may be NULL.
+ * Synchronises the stream. */
+int pasm_get(pasm_ctx* ctx, double* lambda, double* U, int* steps, int* status);
+
+/* pasm_init + pasm_step until no pair is active or opts.max_steps, then
+ * pasm_get.  Returns PASM_ENOTCONV (outputs still written) if pairs remain
+ * active. */
+int pasm_solve(pasm_ctx* ctx, int k, double tol, const double* lambda0, const double* U0,
+               double* lambda_out, double* U_out, int* steps_out, int* status_out);
+
+/* Algorithm 1 step 1 alone: Uhat = result of opts.cycles_per_step V-cycles for
+ * A x = lambda M U started from x = U (all k columns).  lambda (k), U and
+ * Uhat (n x k) host or device.  Does not touch the context's pair state except
+ * for scratch; needs pasm_init with the same k first.  Errors: PASM_ESTATE. */
+int pasm_bvp(pasm_ctx* ctx, const double* lambda, const double* U, double* Uhat);
+
+/* Algorithm 1 step 2 alone: for each column u~ of Uhat, the bordered
+ * eigenproblem on V_H + span{u~}, its selected a-normalised Ritz pair
+ * (lambda_out, U_out) and the bordering scalars beta = a(u~,u~),
+ * zeta = b(u~,u~) (either may be NULL).  lambda_prev (k) is the eigenvalue
+ * the Ritz roots are searched around.  Needs pasm_init with the same k. */
+int pasm_augmented(pasm_ctx* ctx, const double* lambda_prev, const double* Uhat,
+                   double* lambda_out, double* U_out, double* beta, double* zeta);
+
+/* The coarse eigendecomposition computed at setup: Lambda_H (N_H, ascending)
+ * and Q (N_H x N_H row-major, column j = eigenvector j, Q^T M_H Q = I); host
+ * pointers, either may be NULL. */
+int pasm_coarse_eigs(pasm_ctx* ctx, double* lambda_H, double* Q);
+
+/* Sizes: finest n, coarse N_H, number of levels, current k (0 before init). */
+int pasm_sizes(pasm_ctx* ctx, int64_t* n_fine, int32_t* n_coarse, int32_t* n_levels, int32_t* k);
+
+/* Number of kernel launches the last pasm_step issued (graph nodes when a
+ * graph is used). */
+int pasm_last_launches(pasm_ctx* ctx, int* launches);
+
+/* Release the context and all its device memory.  NULL is a no-op. */
+void pasm_destroy(pasm_ctx* ctx);
+
+/* A static string naming a pasm_status code. */
+const char* pasm_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PASM_H */

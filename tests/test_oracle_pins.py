@@ -1,0 +1,344 @@
+"""Pins of the CPU oracle (and of the input fixtures) against what the paper and
+the mathematics fix -- never against the oracle itself.
+
+Each test names the fact it checks.  Together they are chosen so that a
+plausible slip anywhere in the oracle (a dropped term, a wrong sign, a
+transposed operand, a swapped bordering vector, the wrong selection) fails at
+least one of them.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import meshgen as mg
+import oracle
+from oracle import pasm as op
+
+
+def dense_pairs(level, count):
+    """Brute force: the `count` smallest eigenpairs of the FE pencil by the
+    library dense solver, eigenvectors a-normalised."""
+    A, M = level.A.toarray(), level.M.toarray()
+    lam, V = sla.eigh(A, M, subset_by_index=[0, count - 1])
+    V = V / np.sqrt(lam)                 # eigh returns M-normalised: a-norm^2 = lam
+    return lam, V
+
+
+def a_err(prob, ubar, u):
+    """a-norm of ubar - u after aligning the sign of u with ubar."""
+    A = prob.A[-1]
+    s = 1.0 if ubar @ (A @ u) >= 0 else -1.0
+    e = ubar - s * u
+    return float(np.sqrt(e @ (A @ e)))
+
+
+# ----------------------------------------------------------------------------- fixtures (inputs)
+
+def test_p1_stencils_closed_form():
+    """Section 2 discrete pencil: on the (1,1)-split right-triangle mesh the P1
+    stiffness is the 5-point stencil (4, -1) and the mass is 7-point with
+    h^2/2 on the diagonal and h^2/12 on the six edge neighbours."""
+    N = 8
+    h = 1.0 / N
+    lv = mg.assemble(2, N)
+    A, M = lv[0].toarray(), lv[1].toarray()
+    m = N - 1
+    i = 3 + m * 3                        # an interior node far from the boundary
+    nbA = {i: 4.0, i - 1: -1.0, i + 1: -1.0, i - m: -1.0, i + m: -1.0}
+    for j in range(A.shape[1]):
+        assert A[i, j] == pytest.approx(nbA.get(j, 0.0), abs=1e-14)
+    nbM = {i: h * h / 2, i - 1: h * h / 12, i + 1: h * h / 12, i - m: h * h / 12,
+           i + m: h * h / 12, i + m + 1: h * h / 12, i - m - 1: h * h / 12}
+    for j in range(M.shape[1]):
+        assert M[i, j] == pytest.approx(nbM.get(j, 0.0), abs=1e-16)
+
+
+@pytest.mark.parametrize("dim,Nf,Nc", [(2, 32, 4), (3, 16, 4)])
+def test_galerkin_nestedness(dim, Nf, Nc):
+    """Nested spaces V_H in V_h (Section 3.1): for every level,
+    P^T A_h P = A_H and P^T M_h P = M_H, and P reproduces constants on nodes
+    whose coarse parents are interior."""
+    H = mg.build_hierarchy(dim, Nf, Nc)
+    for l, P in enumerate(H.P):
+        Af, Mf = H.levels[l + 1].A, H.levels[l + 1].M
+        Ac, Mc = H.levels[l].A, H.levels[l].M
+        assert abs(P.T @ Af @ P - Ac).max() <= 1e-13 * abs(Ac).max()
+        assert abs(P.T @ Mf @ P - Mc).max() <= 1e-13 * abs(Mc).max()
+        rows = np.asarray(P.sum(axis=1)).ravel()
+        assert np.all(rows <= 1.0 + 1e-15)
+        Nl = H.levels[l + 1].N
+        grid = np.stack(np.meshgrid(*[np.arange(1, Nl)] * dim, indexing="ij")).reshape(dim, -1)
+        grid = grid[:, np.lexsort(grid)]
+        inner = np.all((grid >= 2) & (grid <= Nl - 2), axis=0)
+        assert np.allclose(rows[inner], 1.0, rtol=0, atol=1e-15)
+
+
+def test_discrete_eigenvalues_upper_bound_and_order_h2():
+    """Section 2 upper bound lambda_i <= lambda_{i,h} (min-max) and the O(h^2)
+    eigenvalue convergence to pi^2 (m^2 + n^2) on the unit square: the error
+    ratio under halving h tends to 4."""
+    exact = mg.continuous_eigenvalues(2, 3)
+    errs = []
+    for N in (8, 16, 32):
+        lam, _ = dense_pairs(mg.Level(2, N, *mg.assemble(2, N)), 3)
+        assert np.all(lam >= exact - 1e-12)
+        errs.append(lam - exact)
+    errs = np.array(errs)
+    ratio = errs[1] / errs[2]
+    assert np.all(ratio > 3.6) and np.all(ratio < 4.4)
+
+
+def test_closed_form_3d_first_eigenvalue():
+    """Unit cube, Kuhn mesh: lambda_{1,h} is an upper bound of 3 pi^2 and its
+    error falls about four-fold from h = 1/4 to h = 1/8."""
+    e = []
+    for N in (4, 8):
+        lam, _ = dense_pairs(mg.Level(3, N, *mg.assemble(3, N)), 1)
+        e.append(lam[0] - 3 * np.pi ** 2)
+    assert e[0] > 0 and e[1] > 0
+    assert 3.3 < e[0] / e[1] < 4.5
+
+
+# ----------------------------------------------------------------------------- Algorithm 2 step 1
+
+def test_initial_state_rayleigh_quotient():
+    """Initial pairs (Algorithm 2 step 1 on V_H): u_i = P_c q_i is a-normalised,
+    its Rayleigh quotient on the finest level equals Lambda_H[i] (Galerkin),
+    and Lambda_H[i] >= lambda_{i,h} (min-max on nested spaces)."""
+    H = mg.build_hierarchy(2, 32, 4)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam0, U0 = oracle.initial_state(prob, 5)
+    A, M = H.fine.A, H.fine.M
+    for i in range(5):
+        u = U0[:, i]
+        assert u @ (A @ u) == pytest.approx(1.0, rel=1e-13)
+        assert (u @ (A @ u)) / (u @ (M @ u)) == pytest.approx(lam0[i], rel=1e-13)
+    lam_h, _ = dense_pairs(H.fine, 5)
+    assert np.all(lam0 >= lam_h)
+    with pytest.raises(ValueError):
+        oracle.initial_state(prob, prob.N_H + 1)
+
+
+# ----------------------------------------------------------------------------- Algorithm 1 step 1
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_vcycle_contraction_mesh_independent(N):
+    """Algorithm 1 step 1 by multigrid: the V-cycle error contraction theta < 1
+    (the assumption of Theorem 3.1), uniformly in h; the exact solution is a
+    fixed point of the cycle."""
+    H = mg.build_hierarchy(2, N, 4)
+    prob = oracle.Problem.from_hierarchy(H)
+    A = H.fine.A
+    rng = np.random.default_rng(N)
+    f = rng.standard_normal((A.shape[0], 3))
+    xs = np.column_stack([spla.spsolve(A.tocsc(), f[:, j]) for j in range(3)])
+    x0 = rng.standard_normal(f.shape)
+    x1 = op.vcycle(prob, prob.L, f, x0)
+    for j in range(3):
+        e0, e1 = xs[:, j] - x0[:, j], xs[:, j] - x1[:, j]
+        rate = np.sqrt(e1 @ (A @ e1) / (e0 @ (A @ e0)))
+        assert rate < 0.3
+    xf = op.vcycle(prob, prob.L, f, xs)
+    assert np.abs(xf - xs).max() <= 1e-11 * np.abs(xs).max()
+
+
+def test_coarse_correction_is_a_orthogonal_projection():
+    """Two-level cycle with an exact coarse solve and no post-smoothing: the
+    coarse correction is the a-orthogonal projection onto V_H, so the final
+    residual is orthogonal to V_H (P^T (f - A x) = 0)."""
+    H = mg.build_hierarchy(2, 16, 8)
+    prob = oracle.Problem.from_hierarchy(H, nu_post=0)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((H.fine.n, 2))
+    x = op.vcycle(prob, prob.L, f, rng.standard_normal((H.fine.n, 2)))
+    r = H.P[0].T @ (f - H.fine.A @ x)
+    assert np.abs(r).max() <= 1e-12 * np.abs(H.P[0].T @ f).max()
+
+
+def test_bvp_solve_is_two_vcycles_from_u():
+    """Algorithm 1 step 1 with the readings stated in the oracle: the right-hand
+    side is lambda M u and the multigrid iteration starts from u; two cycles
+    equal two applications of one cycle."""
+    H = mg.build_hierarchy(2, 16, 4)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, 2)
+    Ut = op.bvp_solve(prob, lam, U)
+    f = (H.fine.M @ U) * lam
+    x = op.vcycle(prob, prob.L, f, U.copy())
+    x = op.vcycle(prob, prob.L, f, x)
+    assert np.array_equal(x, Ut)
+
+
+# ----------------------------------------------------------------------------- Algorithm 1 step 2
+
+def test_bordered_pencil_is_ritz_projection():
+    """The bordered matrices of Section 3.1 are the Galerkin projection of the
+    finest pencil onto V_H + span{u~}: with Z = [P_c, u~], Z^T A Z and Z^T M Z
+    (computed densely here) equal [[A_H, b], [b^T, beta]] and
+    [[M_H, c], [c^T, zeta]]."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, 3)
+    Ut = op.bvp_solve(prob, lam, U)
+    Z = np.column_stack([prob.Pc.toarray(), Ut[:, 2]])
+    Ad, Md = H.fine.A.toarray(), H.fine.M.toarray()
+    b, c, beta, zeta = op.bordering(prob, Ut[:, 2])
+    ZA = Z.T @ Ad @ Z
+    ZM = Z.T @ Md @ Z
+    N = prob.N_H
+    assert np.allclose(ZA[:N, N], b, rtol=1e-12, atol=1e-13)
+    assert np.allclose(ZM[:N, N], c, rtol=1e-12, atol=1e-16)
+    assert ZA[N, N] == pytest.approx(beta, rel=1e-12)
+    assert ZM[N, N] == pytest.approx(zeta, rel=1e-12)
+    assert np.allclose(ZA[:N, :N], prob.A_H, atol=1e-12)
+    assert np.allclose(ZM[:N, :N], prob.M_H, atol=1e-16)
+
+
+def test_ritz_values_bound_and_interlace():
+    """Ritz values of V_H + span{u~}: the j-th is an upper bound of the j-th
+    discrete eigenvalue (min-max), and they interlace with Lambda_H (Cauchy,
+    one added dimension)."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, 4)
+    Ut = op.bvp_solve(prob, lam, U)
+    lamH, _ = oracle.coarse_eigenpairs(prob)
+    lam_h, _ = dense_pairs(H.fine, prob.N_H + 1)
+    for i in range(4):
+        theta, X, sv, ok = op.augmented_eigenproblem(prob, Ut[:, i])
+        assert ok
+        assert np.all(theta >= lam_h * (1 - 1e-12))
+        assert np.all(theta[:-1] <= lamH * (1 + 1e-12))
+        assert np.all(theta[1:] >= lamH * (1 - 1e-12))
+        # a-normalisation of every Ritz vector, checked on the finest level
+        W = prob.Pc @ X[:-1] + np.outer(Ut[:, i], X[-1])
+        assert np.allclose(np.einsum("ij,ij->j", W, H.fine.A @ W), 1.0, rtol=1e-10)
+
+
+def test_exact_eigenpair_is_fixed_point():
+    """A discrete eigenpair is a fixed point of Correction: the multigrid
+    iterate of an exact pair is the pair itself and the selected Ritz pair
+    returns it (lambda to 1e-12, the vector to 1e-10 in the a-norm)."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, V = dense_pairs(H.fine, 4)
+    lam_new, U_new, info = oracle.correction(prob, lam, V)
+    assert np.allclose(lam_new, lam, rtol=1e-12)
+    for i in range(4):
+        assert a_err(prob, V[:, i], U_new[:, i]) < 1e-10
+
+
+def test_selection_picks_largest_component():
+    """Selection rule of Section 3.1: the chosen Ritz vector maximises
+    |b(u_{H,h}, u~)|; u~ built as (eigvec 3) + small multiples of others must
+    select eigenvalue 3, and flipping the sign of u~ keeps the same pair with
+    b(u_new, u~) > 0."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, V = dense_pairs(H.fine, 6)
+    ut = V[:, 3] + 0.05 * V[:, 0] + 0.05 * V[:, 5]
+    theta, X, sv, ok = op.augmented_eigenproblem(prob, ut)
+    j = int(np.argmax(np.abs(sv)))
+    assert theta[j] == pytest.approx(lam[3], rel=1e-3)
+    M = H.fine.M
+    for sgn in (1.0, -1.0):
+        lam_new, U_new, info = oracle.correction(prob, np.array([lam[3]]), sgn * V[:, 3:4])
+        assert (U_new[:, 0] @ (M @ (sgn * V[:, 3]))) > 0
+
+
+# ----------------------------------------------------------------------------- Algorithm 2 (whole iteration)
+
+@pytest.mark.parametrize("Nf,Nc,k", [(16, 4, 2), (32, 8, 5), (64, 8, 5)])
+def test_converged_pairs_match_brute_force(Nf, Nc, k):
+    """Converged PASM eigenvalues equal the k smallest discrete eigenvalues of
+    the brute-force dense solve to 1e-12 and the vectors to 1e-8 (a-norm)."""
+    H = mg.build_hierarchy(2, Nf, Nc)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U, steps, _ = oracle.solve(prob, k, tol=1e-13, max_steps=80)
+    lam_ref, V = dense_pairs(H.fine, k)
+    assert np.allclose(lam, lam_ref, rtol=2e-12)
+    for i in range(k):
+        assert a_err(prob, V[:, i], U[:, i]) < 1e-6
+
+
+def test_first_pair_monotone_and_error_bound():
+    """For the first pair the eigenvalue sequence decreases monotonically, its
+    error is bounded by lambda ||ubar - u||_a^2 (the eigenvalue estimate of
+    Theorem 3.2), and the a-norm error contracts every step (Theorem 3.1)."""
+    H = mg.build_hierarchy(2, 32, 4)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam_ref, V = dense_pairs(H.fine, 1)
+    lam, U = oracle.initial_state(prob, 1)
+    prev_lam, prev_err = lam[0], a_err(prob, V[:, 0], U[:, 0])
+    for _ in range(6):
+        lam, U, _ = oracle.correction(prob, lam, U)
+        err = a_err(prob, V[:, 0], U[:, 0])
+        assert lam[0] <= prev_lam * (1 + 1e-14)
+        assert lam[0] - lam_ref[0] <= lam[0] * err ** 2 * (1 + 1e-8) + 1e-13
+        if prev_err > 1e-9:
+            assert err < prev_err
+        prev_lam, prev_err = lam[0], err
+
+
+def test_contraction_rate_mesh_independent():
+    """Theorem 3.1: the per-step a-norm contraction of the first pair is below 1
+    and about the same on h = 1/32 and h = 1/64 with the same V_H."""
+    rates = []
+    for N in (32, 64):
+        H = mg.build_hierarchy(2, N, 8)
+        prob = oracle.Problem.from_hierarchy(H)
+        lam_ref, V = dense_pairs(H.fine, 1)
+        lam, U = oracle.initial_state(prob, 1)
+        errs = [a_err(prob, V[:, 0], U[:, 0])]
+        for _ in range(3):
+            lam, U, _ = oracle.correction(prob, lam, U)
+            errs.append(a_err(prob, V[:, 0], U[:, 0]))
+        rates.append(errs[3] / errs[2])
+    assert max(rates) < 0.5
+    assert 0.33 < rates[0] / rates[1] < 3.0
+
+
+def test_pairs_independent_batch_equals_single():
+    """Section 3.2: the pairs exchange no data, so running k pairs together
+    equals running each pair alone (up to the blocking order of the library's
+    dense triangular solves, 1e-13)."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, 4)
+    lb, Ub, _ = oracle.correction(prob, lam, U)
+    for i in range(4):
+        li, Ui, _ = oracle.correction(prob, lam[i:i + 1], U[:, i:i + 1])
+        assert li[0] == pytest.approx(lb[i], rel=1e-13)
+        assert np.abs(Ui[:, 0] - Ub[:, i]).max() <= 1e-11 * np.abs(Ub[:, i]).max()
+
+
+def test_orthogonality_improves_with_steps():
+    """Remark on orthogonality: max |b(u_i, u_j)| over i != j (b-normalised)
+    shrinks as the number of finest-level correction steps grows."""
+    H = mg.build_hierarchy(2, 32, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    M = H.fine.M
+
+    def worst(U):
+        G = U.T @ (M @ U)
+        d = np.sqrt(np.diag(G))
+        G = G / d[:, None] / d[None, :]
+        return np.abs(G - np.diag(np.diag(G))).max()
+
+    lam, U = oracle.initial_state(prob, 4)
+    lam, U, _ = oracle.correction(prob, lam, U)
+    w1 = worst(U)
+    for _ in range(5):
+        lam, U, _ = oracle.correction(prob, lam, U)
+    assert worst(U) < 1e-2 * w1
+
+
+def test_frozen_pairs_do_not_change():
+    """A pair whose relative eigenvalue change fell below tol is frozen: later
+    steps leave its eigenvalue and vector untouched."""
+    H = mg.build_hierarchy(2, 16, 4)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U, steps, hist = oracle.solve(prob, 2, tol=1e-6, max_steps=30, history=True)
+    lam2, U2, steps2, _ = oracle.solve(prob, 2, tol=1e-6, max_steps=60)
+    assert np.array_equal(steps, steps2) and np.array_equal(lam, lam2)
