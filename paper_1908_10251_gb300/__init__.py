@@ -1,0 +1,13 @@
+"""GB300 (sm_103a) implementation of the parallel augmented subspace method
+(PASM) for A u = lambda M u: batched correction steps for k eigenpairs in
+hand-written CUDA kernels behind the C ABI of include/pasm.h.
+
+`capi` is the ctypes binding (one function per C entry point); `build`
+compiles libpasm.so in-tree.
+"""
+from . import capi  # noqa: F401
+from .capi import (  # noqa: F401
+    pasm_default_opts, pasm_setup, pasm_init, pasm_step, pasm_step_async, pasm_get, pasm_solve, pasm_bvp,
+    pasm_augmented, pasm_coarse_eigs, pasm_sizes, pasm_last_launches, pasm_destroy, pasm_strerror,
+    PasmError, load_library,
+)

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of libpasm (include/pasm.h), one Python function per
+C entry point with the same name.  Argument marshalling only: every step of
+the method runs in the library's CUDA kernels.  There is no fallback: if the
+shared library is missing or fails to load, every call raises.
+
+Arrays may be numpy arrays (host memory) or torch CUDA tensors (device
+memory); block vectors are n x k row-major float64, eigenvalues float64,
+per-pair counters int32.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpasm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pasm.h")
+
+PASM_OK, PASM_EINVAL, PASM_EK_TOO_BIG, PASM_ENOMEM, PASM_ECUDA = 0, 1, 2, 3, 4
+PASM_ENOTCONV, PASM_EDEGENERATE, PASM_ENAN, PASM_ESTATE, PASM_ENOTPD = 5, 6, 7, 8, 9
+PASM_PAIR_ACTIVE, PASM_PAIR_CONVERGED, PASM_PAIR_DEGENERATE, PASM_PAIR_NAN = 0, 1, 2, 3
+PASM_FP64, PASM_MIXED = 0, 1
+PASM_SCORE_A, PASM_SCORE_B = 0, 1
+PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
+
+
+class pasm_csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class pasm_opts(ctypes.Structure):
+    _fields_ = [("omega", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
+                ("cycles_per_step", ctypes.c_int), ("max_steps", ctypes.c_int), ("precision", ctypes.c_int),
+                ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class PasmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s: %s (status %d)" % (where, pasm_strerror(code), code))
+        self.code = code
+
+
+_lib = None
+
+
+def header_symbols():
+    """Names of the functions include/pasm.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(pasm_\w+)\s*\(", text, re.M)))
+
+
+def load_library():
+    """Load libpasm.so (built by paper_1908_10251_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpasm.so is not built (%s); run `python -m paper_1908_10251_gb300.build`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    sig = {
+        "pasm_default_opts": (None, [ctypes.POINTER(pasm_opts)]),
+        "pasm_setup": (I, [ctypes.POINTER(P), I, ctypes.POINTER(pasm_csr), ctypes.POINTER(pasm_csr),
+                           ctypes.POINTER(pasm_csr), ctypes.POINTER(pasm_opts), P]),
+        "pasm_init": (I, [P, I, ctypes.c_double, P, P]),
+        "pasm_step": (I, [P, ctypes.POINTER(I)]),
+        "pasm_get": (I, [P, P, P, P, P]),
+        "pasm_solve": (I, [P, I, ctypes.c_double, P, P, P, P, P, P]),
+        "pasm_bvp": (I, [P, P, P, P]),
+        "pasm_augmented": (I, [P, P, P, P, P, P, P]),
+        "pasm_coarse_eigs": (I, [P, P, P]),
+        "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
+        "pasm_destroy": (None, [P]),
+        "pasm_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype=np.float64):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):                       # torch tensor
+        want = {np.float64: "torch.float64", np.int32: "torch.int32"}[dtype]
+        if str(a.dtype) != want or not a.is_contiguous():
+            raise TypeError("tensor must be contiguous %s" % want)
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("array must be a C-contiguous numpy %s array" % np.dtype(dtype))
+    return a.ctypes.data
+
+
+def _check(code: int, where: str, allow=()):
+    if code != PASM_OK and code not in allow:
+        raise PasmError(code, where)
+    return code
+
+
+class Context:
+    """Owns a pasm_ctx* and the host copies handed to pasm_setup."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            pasm_destroy(self)
+        except Exception:
+            pass
+
+
+def _csr(m):
+    indptr = np.ascontiguousarray(m.indptr, dtype=np.int32)
+    indices = np.ascontiguousarray(m.indices, dtype=np.int32)
+    data = np.ascontiguousarray(m.data, dtype=np.float64)
+    s = pasm_csr(int(m.shape[0]), int(m.shape[1]), int(data.size), indptr.ctypes.data,
+                 indices.ctypes.data if data.size else None, data.ctypes.data if data.size else None)
+    return s, (indptr, indices, data)
+
+
+def pasm_default_opts(**overrides) -> pasm_opts:
+    o = pasm_opts()
+    load_library().pasm_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def pasm_setup(A, M, P, opts=None, stream=None) -> Context:
+    """A, M: per-level CSR matrices (coarsest first), P: interpolations
+    P[l]: level l -> l+1; objects with indptr/indices/data/shape (scipy CSR)."""
+    lib = load_library()
+    L = len(A)
+    keep = []
+    arrA = (pasm_csr * L)(); arrM = (pasm_csr * L)(); arrP = (pasm_csr * max(L - 1, 1))()
+    for l in range(L):
+        arrA[l], k1 = _csr(A[l]); arrM[l], k2 = _csr(M[l]); keep += [k1, k2]
+    for l in range(L - 1):
+        arrP[l], k3 = _csr(P[l]); keep.append(k3)
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else pasm_default_opts()
+    _check(lib.pasm_setup(ctypes.byref(h), L, arrA, arrM, arrP, ctypes.byref(o), stream), "pasm_setup")
+    return Context(h, keep)
+
+
+def pasm_init(ctx: Context, k: int, tol: float, lambda0=None, U0=None):
+    _check(load_library().pasm_init(ctx.handle, k, tol, _ptr(lambda0), _ptr(U0)), "pasm_init")
+
+
+def pasm_step(ctx: Context) -> int:
+    n = ctypes.c_int(0)
+    _check(load_library().pasm_step(ctx.handle, ctypes.byref(n)), "pasm_step")
+    return n.value
+
+
+def pasm_step_async(ctx: Context):
+    """pasm_step without reading the active count back (no synchronisation)."""
+    _check(load_library().pasm_step(ctx.handle, None), "pasm_step")
+
+
+def pasm_get(ctx: Context, lam=None, U=None, steps=None, status=None):
+    _check(load_library().pasm_get(ctx.handle, _ptr(lam), _ptr(U), _ptr(steps, np.int32), _ptr(status, np.int32)),
+           "pasm_get")
+
+
+def pasm_solve(ctx: Context, k: int, tol: float, lambda0=None, U0=None, lambda_out=None, U_out=None,
+               steps_out=None, status_out=None) -> int:
+    return _check(load_library().pasm_solve(ctx.handle, k, tol, _ptr(lambda0), _ptr(U0), _ptr(lambda_out),
+                                            _ptr(U_out), _ptr(steps_out, np.int32), _ptr(status_out, np.int32)),
+                  "pasm_solve", allow=(PASM_ENOTCONV,))
+
+
+def pasm_bvp(ctx: Context, lam, U, Uhat):
+    _check(load_library().pasm_bvp(ctx.handle, _ptr(lam), _ptr(U), _ptr(Uhat)), "pasm_bvp")
+
+
+def pasm_augmented(ctx: Context, lam_prev, Uhat, lambda_out=None, U_out=None, beta=None, zeta=None):
+    _check(load_library().pasm_augmented(ctx.handle, _ptr(lam_prev), _ptr(Uhat), _ptr(lambda_out), _ptr(U_out),
+                                         _ptr(beta), _ptr(zeta)), "pasm_augmented")
+
+
+def pasm_sizes(ctx: Context):
+    n = ctypes.c_int64(); nh = ctypes.c_int32(); nl = ctypes.c_int32(); k = ctypes.c_int32()
+    _check(load_library().pasm_sizes(ctx.handle, ctypes.byref(n), ctypes.byref(nh), ctypes.byref(nl),
+                                     ctypes.byref(k)), "pasm_sizes")
+    return n.value, nh.value, nl.value, k.value
+
+
+def pasm_coarse_eigs(ctx: Context):
+    _, nh, _, _ = pasm_sizes(ctx)
+    lam = np.zeros(nh)
+    Q = np.zeros((nh, nh))
+    _check(load_library().pasm_coarse_eigs(ctx.handle, lam.ctypes.data, Q.ctypes.data), "pasm_coarse_eigs")
+    return lam, Q
+
+
+def pasm_last_launches(ctx: Context) -> int:
+    n = ctypes.c_int(0)
+    _check(load_library().pasm_last_launches(ctx.handle, ctypes.byref(n)), "pasm_last_launches")
+    return n.value
+
+
+def pasm_destroy(ctx: Context):
+    if ctx.handle is not None and ctx.handle.value:
+        load_library().pasm_destroy(ctx.handle)
+    ctx.handle = ctypes.c_void_p()
+
+
+def pasm_strerror(code: int) -> str:
+    try:
+        return load_library().pasm_strerror(code).decode()
+    except Exception:
+        return "status %d" % code

@@ -1,0 +1,478 @@
+// Device kernels of the PASM correction step on sm_103a.
+//
+// Block vectors are n x ldk row-major (ldk = k rounded up to a power of two
+// >= 4), so a gathered column index of a CSR row yields ldk contiguous values
+// and every matrix entry is reused ldk times (all pairs of Algorithm 1 share
+// the same matrices; Section 3.2 runs them independently).  A "row group" of
+// tpr threads owns one row, each thread CH chunks of one 16-byte vector.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+namespace pasm {
+
+static constexpr int kBlock = 256;
+
+struct Geo {
+  int tpr, ch;
+};
+template <typename T>
+static Geo geometry(int ldk) {
+  const int V = Vec16<T>::N;
+  int chunks = ldk / V;
+  Geo g;
+  if (chunks <= 32) { g.tpr = chunks; g.ch = 1; }
+  else { g.tpr = 32; g.ch = chunks / 32; }
+  return g;
+}
+
+#define PASM_DISPATCH_CH(ch, ...)                          \
+  switch (ch) {                                            \
+    case 1: { constexpr int CH = 1; __VA_ARGS__; } break;  \
+    case 2: { constexpr int CH = 2; __VA_ARGS__; } break;  \
+    case 4: { constexpr int CH = 4; __VA_ARGS__; } break;  \
+    default: break;                                        \
+  }
+
+// ----------------------------------------------------------------------------------------------
+// Generic row operation (Jacobi sweep, residual, SpMM, SpMM + add).
+template <typename T, int CH, int OP>
+__global__ void __launch_bounds__(kBlock) k_rowop(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const T* __restrict__ av, const T* __restrict__ X,
+                                                   const T* Y, const T* Z, const T* __restrict__ dinv, T omega,
+                                                   T* out, int ldk, int tpr) {
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  T acc[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[c][v] = T(0);
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = __ldg(ci + p);
+    const T a = __ldg(av + p);
+    const T* xr = X + (size_t)j * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      T x[V];
+      ldg16<T>(xr + (c * tpr + lane) * V, x);
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[c][v] = fma(a, x[v], acc[c][v]);
+    }
+  }
+  const size_t base = (size_t)row * ldk;
+  T w = T(0);
+  if (OP == OP_JACOBI) w = omega * dinv[row];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const size_t off = base + (c * tpr + lane) * V;
+    T r[V];
+    if (OP == OP_JACOBI) {
+      T y[V], z[V];
+      Vec16<T>::load(Y + off, y);
+      Vec16<T>::load(Z + off, z);
+#pragma unroll
+      for (int v = 0; v < V; ++v) r[v] = fma(w, y[v] - acc[c][v], z[v]);
+    } else if (OP == OP_RESID) {
+      T y[V];
+      Vec16<T>::load(Y + off, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) r[v] = y[v] - acc[c][v];
+    } else if (OP == OP_SPMM) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) r[v] = acc[c][v];
+    } else {
+      T y[V];
+      Vec16<T>::load(Y + off, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) r[v] = y[v] + acc[c][v];
+    }
+    Vec16<T>::store(out + off, r);
+  }
+}
+
+template <typename T>
+void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, const T* Z, const T* dinv, T omega,
+           T* out, int ldk) {
+  if (S.n_rows == 0) return;
+  Geo g = geometry<T>(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (S.n_rows + rpb - 1) / rpb;
+  const T* av = vals<T>(S);
+  PASM_DISPATCH_CH(g.ch,
+    switch (op) {
+      case OP_JACOBI: k_rowop<T, CH, OP_JACOBI><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
+      case OP_RESID: k_rowop<T, CH, OP_RESID><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
+      case OP_SPMM: k_rowop<T, CH, OP_SPMM><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
+      case OP_SPMM_ADD: k_rowop<T, CH, OP_SPMM_ADD><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
+    });
+  L.bump();
+}
+template void rowop<double>(const Launch&, RowOp, const DCsr&, const double*, const double*, const double*,
+                            const double*, double, double*, int);
+template void rowop<float>(const Launch&, RowOp, const DCsr&, const float*, const float*, const float*,
+                           const float*, float, float*, int);
+
+// ----------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_jacobi_zero(int64_t total, int ldk, const T* __restrict__ dinv, T omega, const T* __restrict__ F,
+                              T* __restrict__ out) {
+  constexpr int V = Vec16<T>::N;
+  const int64_t nv = total / V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i * V;
+    const int64_t row = e / ldk;
+    const T w = omega * dinv[row];
+    T f[V], r[V];
+    Vec16<T>::load(F + e, f);
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = w * f[v];
+    Vec16<T>::store(out + e, r);
+  }
+}
+
+template <typename T>
+void jacobi_zero(const Launch& L, int n, const T* dinv, T omega, const T* F, T* out, int ldk) {
+  if (n == 0) return;
+  const int64_t total = (int64_t)n * ldk;
+  const int64_t nv = total / Vec16<T>::N;
+  int grid = (int)std::min<int64_t>((nv + kBlock - 1) / kBlock, 152 * 16);
+  k_jacobi_zero<T><<<grid, kBlock, 0, L.s>>>(total, ldk, dinv, omega, F, out);
+  L.bump();
+}
+template void jacobi_zero<double>(const Launch&, int, const double*, double, const double*, double*, int);
+template void jacobi_zero<float>(const Launch&, int, const float*, float, const float*, float*, int);
+
+// ----------------------------------------------------------------------------------------------
+// Outer float64 kernels of the defect correction.
+template <typename TV> __device__ __forceinline__ void store_vec2(TV* p, double a, double b);
+template <> __device__ __forceinline__ void store_vec2<double>(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+template <> __device__ __forceinline__ void store_vec2<float>(float* p, double a, double b) {
+  *reinterpret_cast<float2*>(p) = make_float2((float)a, (float)b);
+}
+template <typename TV> __device__ __forceinline__ void load_vec2(const TV* p, double* v);
+template <> __device__ __forceinline__ void load_vec2<double>(const double* p, double* v) {
+  double2 t = *reinterpret_cast<const double2*>(p); v[0] = t.x; v[1] = t.y;
+}
+template <> __device__ __forceinline__ void load_vec2<float>(const float* p, double* v) {
+  float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y;
+}
+
+// One row, float64 gather of S X over CH chunks of 2 columns.
+template <int CH>
+__device__ __forceinline__ void gather_row64(const int* __restrict__ rp, const int* __restrict__ ci,
+                                             const double* __restrict__ av, const double* __restrict__ X, int row,
+                                             int lane, int tpr, int ldk, double (&acc)[CH][2]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c) acc[c][0] = acc[c][1] = 0.0;
+  const int p0 = rp[row], p1 = rp[row + 1];
+  for (int p = p0; p < p1; ++p) {
+    const int j = __ldg(ci + p);
+    const double a = __ldg(av + p);
+    const double* xr = X + (size_t)j * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      double x[2];
+      ldg16<double>(xr + (c * tpr + lane) * 2, x);
+      acc[c][0] = fma(a, x[0], acc[c][0]);
+      acc[c][1] = fma(a, x[1], acc[c][1]);
+    }
+  }
+}
+
+template <typename TV, int CH>
+__global__ void __launch_bounds__(kBlock) k_outer_rhs_res(int n, const int* __restrict__ arp, const int* __restrict__ aci,
+                                                           const double* __restrict__ aval, const int* __restrict__ mrp,
+                                                           const int* __restrict__ mci, const double* __restrict__ mval,
+                                                           const double* __restrict__ lam, const double* __restrict__ U,
+                                                           double* __restrict__ Fd, TV* __restrict__ R, int ldk, int tpr) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  double mu[CH][2], au[CH][2];
+  gather_row64<CH>(mrp, mci, mval, U, row, lane, tpr, ldk, mu);
+  gather_row64<CH>(arp, aci, aval, U, row, lane, tpr, ldk, au);
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    const double f0 = lam[col] * mu[c][0], f1 = lam[col + 1] * mu[c][1];
+    *reinterpret_cast<double2*>(Fd + base + col) = make_double2(f0, f1);
+    store_vec2<TV>(R + base + col, f0 - au[c][0], f1 - au[c][1]);
+  }
+}
+
+template <typename TV, int CH>
+__global__ void __launch_bounds__(kBlock) k_outer_res(int n, const int* __restrict__ arp, const int* __restrict__ aci,
+                                                       const double* __restrict__ aval, const double* __restrict__ Fd,
+                                                       const double* __restrict__ X, TV* __restrict__ R, int ldk, int tpr) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  double ax[CH][2];
+  gather_row64<CH>(arp, aci, aval, X, row, lane, tpr, ldk, ax);
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    double2 f = *reinterpret_cast<const double2*>(Fd + base + col);
+    store_vec2<TV>(R + base + col, f.x - ax[c][0], f.y - ax[c][1]);
+  }
+}
+
+template <typename TV>
+__global__ void k_outer_axpy(int64_t total, const double* B, const TV* __restrict__ E, double* X) {
+  const int64_t np = total / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    double e[2];
+    load_vec2<TV>(E + 2 * i, e);
+    double2 b = *reinterpret_cast<const double2*>(B + 2 * i);
+    *reinterpret_cast<double2*>(X + 2 * i) = make_double2(b.x + e[0], b.y + e[1]);
+  }
+}
+
+static Geo geometry64(int ldk) { return geometry<double>(ldk); }
+
+template <typename TV>
+void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
+                        double* Fd, TV* R, int ldk) {
+  Geo g = geometry64(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  PASM_DISPATCH_CH(g.ch, k_outer_rhs_res<TV, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, M.rp, M.ci,
+                                                                            M.v64, lam, U, Fd, R, ldk, g.tpr));
+  L.bump();
+}
+template <typename TV>
+void outer_residual(const Launch& L, const DCsr& A, const double* Fd, const double* X, TV* R, int ldk) {
+  Geo g = geometry64(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  PASM_DISPATCH_CH(g.ch, k_outer_res<TV, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, Fd, X, R, ldk,
+                                                                        g.tpr));
+  L.bump();
+}
+template <typename TV>
+void outer_axpy(const Launch& L, int n, const double* B, const TV* E, double* X, int ldk) {
+  const int64_t total = (int64_t)n * ldk;
+  int grid = (int)std::min<int64_t>((total / 2 + kBlock - 1) / kBlock, 152 * 16);
+  k_outer_axpy<TV><<<grid, kBlock, 0, L.s>>>(total, B, E, X);
+  L.bump();
+}
+template void outer_rhs_residual<double>(const Launch&, const DCsr&, const DCsr&, const double*, const double*,
+                                         double*, double*, int);
+template void outer_rhs_residual<float>(const Launch&, const DCsr&, const DCsr&, const double*, const double*,
+                                        double*, float*, int);
+template void outer_residual<double>(const Launch&, const DCsr&, const double*, const double*, double*, int);
+template void outer_residual<float>(const Launch&, const DCsr&, const double*, const double*, float*, int);
+template void outer_axpy<double>(const Launch&, int, const double*, const double*, double*, int);
+template void outer_axpy<float>(const Launch&, int, const double*, const float*, double*, int);
+
+// ----------------------------------------------------------------------------------------------
+// Bordering (the matrix form of Section 3.1): YA = A u~, YM = M u~ and the
+// column dot products beta = u~^T A u~, zeta = u~^T M u~ as per-block partials.
+template <int CH>
+__global__ void __launch_bounds__(kBlock) k_border(int n, const int* __restrict__ arp, const int* __restrict__ aci,
+                                                    const double* __restrict__ aval, const int* __restrict__ mrp,
+                                                    const int* __restrict__ mci, const double* __restrict__ mval,
+                                                    const double* __restrict__ X, double* __restrict__ YA,
+                                                    double* __restrict__ YM, double* __restrict__ partials, int ldk,
+                                                    int tpr) {
+  extern __shared__ double red[];  // [rpb][2][ldk]
+  const int rpb = kBlock / tpr;
+  const int grp = threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  double sA[CH][2], sM[CH][2];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) sA[c][0] = sA[c][1] = sM[c][0] = sM[c][1] = 0.0;
+  for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
+    double ya[CH][2], ym[CH][2];
+    gather_row64<CH>(arp, aci, aval, X, row, lane, tpr, ldk, ya);
+    gather_row64<CH>(mrp, mci, mval, X, row, lane, tpr, ldk, ym);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int col = (c * tpr + lane) * 2;
+      double2 x = *reinterpret_cast<const double2*>(X + base + col);
+      *reinterpret_cast<double2*>(YA + base + col) = make_double2(ya[c][0], ya[c][1]);
+      *reinterpret_cast<double2*>(YM + base + col) = make_double2(ym[c][0], ym[c][1]);
+      sA[c][0] = fma(x.x, ya[c][0], sA[c][0]);
+      sA[c][1] = fma(x.y, ya[c][1], sA[c][1]);
+      sM[c][0] = fma(x.x, ym[c][0], sM[c][0]);
+      sM[c][1] = fma(x.y, ym[c][1], sM[c][1]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    red[(grp * 2 + 0) * ldk + col] = sA[c][0];
+    red[(grp * 2 + 0) * ldk + col + 1] = sA[c][1];
+    red[(grp * 2 + 1) * ldk + col] = sM[c][0];
+    red[(grp * 2 + 1) * ldk + col + 1] = sM[c][1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * ldk; t += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += red[r * 2 * ldk + t];
+    partials[(size_t)blockIdx.x * 2 * ldk + t] = s;
+  }
+}
+
+int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
+                    double* partials, int ldk, int max_blocks) {
+  Geo g = geometry64(ldk);
+  const int rpb = kBlock / g.tpr;
+  int grid = std::min((A.n_rows + rpb - 1) / rpb, max_blocks);
+  if (grid < 1) grid = 1;
+  const size_t smem = (size_t)rpb * 2 * ldk * sizeof(double);
+  PASM_DISPATCH_CH(g.ch, k_border<CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, M.rp, M.ci, M.v64, X,
+                                                                    YA, YM, partials, ldk, g.tpr));
+  L.bump();
+  return grid;
+}
+
+__global__ void k_colsum(const double* __restrict__ partials, int nblk, int width, double* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= width) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * width + t];
+  out[t] = s;
+}
+
+void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out) {
+  const int width = nq * ldk;
+  k_colsum<<<(width + 127) / 128, 128, 0, L.s>>>(partials, nblk, width, out);
+  L.bump();
+}
+
+// ----------------------------------------------------------------------------------------------
+// Small dense products on the coarse space (N_H x N_H times N_H x ldk).
+template <typename T>
+__global__ void k_dense_mm(int m, int p, const T* __restrict__ D, int ldd, int trans, const T* __restrict__ B,
+                           T* __restrict__ C, int ldk) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (c >= ldk || i >= m) return;
+  T s = T(0);
+  if (trans) {
+    for (int j = 0; j < p; ++j) s = fma(D[(size_t)j * ldd + i], B[(size_t)j * ldk + c], s);
+  } else {
+    const T* d = D + (size_t)i * ldd;
+    for (int j = 0; j < p; ++j) s = fma(d[j], B[(size_t)j * ldk + c], s);
+  }
+  C[(size_t)i * ldk + c] = s;
+}
+
+template <typename T>
+void dense_mm(const Launch& L, int m, int p, const T* D, int ldd, bool trans, const T* B, T* C, int ldk) {
+  dim3 grid((ldk + 63) / 64, m);
+  k_dense_mm<T><<<grid, 64, 0, L.s>>>(m, p, D, ldd, trans ? 1 : 0, B, C, ldk);
+  L.bump();
+}
+template void dense_mm<double>(const Launch&, int, int, const double*, int, bool, const double*, double*, int);
+template void dense_mm<float>(const Launch&, int, int, const float*, int, bool, const float*, float*, int);
+
+__global__ void k_coarse_init(int NH, int k, const double* __restrict__ Q, const double* __restrict__ lamH,
+                              double* __restrict__ W0, double* __restrict__ lam, int ldk) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (c >= ldk) return;
+  W0[(size_t)j * ldk + c] = c < k ? Q[(size_t)j * NH + c] / sqrt(lamH[c]) : 0.0;
+  if (j == 0) lam[c] = c < k ? lamH[c] : 1.0;
+}
+
+void coarse_init(const Launch& L, int NH, int k, const double* Q, const double* lamH, double* W0, double* lam,
+                 int ldk) {
+  dim3 grid((ldk + 63) / 64, NH);
+  k_coarse_init<<<grid, 64, 0, L.s>>>(NH, k, Q, lamH, W0, lam, ldk);
+  L.bump();
+}
+
+// ----------------------------------------------------------------------------------------------
+// Update u^(l+1) = alpha u~ + P_c u_H (Algorithm 1, output of step 2), the last
+// prolongation fused with the combination.
+template <int CH>
+__global__ void __launch_bounds__(kBlock) k_update(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                    const double* __restrict__ pv, const double* __restrict__ W,
+                                                    const double* __restrict__ X, const double* __restrict__ alpha,
+                                                    const int* __restrict__ upd, double* __restrict__ U, int ldk,
+                                                    int tpr, int identity) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  double pw[CH][2];
+  if (identity) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      double2 w = *reinterpret_cast<const double2*>(W + (size_t)row * ldk + (c * tpr + lane) * 2);
+      pw[c][0] = w.x; pw[c][1] = w.y;
+    }
+  } else {
+    gather_row64<CH>(rp, ci, pv, W, row, lane, tpr, ldk, pw);
+  }
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    double2 x = *reinterpret_cast<const double2*>(X + base + col);
+    double2 u = *reinterpret_cast<const double2*>(U + base + col);
+    if (upd[col]) u.x = fma(alpha[col], x.x, pw[c][0]);
+    if (upd[col + 1]) u.y = fma(alpha[col + 1], x.y, pw[c][1]);
+    *reinterpret_cast<double2*>(U + base + col) = u;
+  }
+}
+
+void update_pairs(const Launch& L, const DCsr& P, const double* W, const double* X, const double* alpha,
+                  const int* upd, double* U, int ldk) {
+  Geo g = geometry64(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (P.n_rows + rpb - 1) / rpb;
+  PASM_DISPATCH_CH(g.ch, k_update<CH><<<grid, kBlock, 0, L.s>>>(P.n_rows, P.rp, P.ci, P.v64, W, X, alpha, upd, U,
+                                                                 ldk, g.tpr, 0));
+  L.bump();
+}
+void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
+                           const int* upd, double* U, int ldk) {
+  Geo g = geometry64(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (n + rpb - 1) / rpb;
+  PASM_DISPATCH_CH(g.ch, k_update<CH><<<grid, kBlock, 0, L.s>>>(n, nullptr, nullptr, nullptr, W, X, alpha, upd, U,
+                                                                 ldk, g.tpr, 1));
+  L.bump();
+}
+
+__global__ void k_count_active(const int* __restrict__ active, int k, int* out) {
+  int c = 0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) c += active[i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (threadIdx.x == 0) *out = c;
+}
+void count_active(const Launch& L, const int* active, int k, int* out) {
+  k_count_active<<<1, 32, 0, L.s>>>(active, k, out);
+  L.bump();
+}
+
+__global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+void cast_d2f(const Launch& L, const double* in, float* out, int64_t count) {
+  if (count == 0) return;
+  int grid = (int)std::min<int64_t>((count + kBlock - 1) / kBlock, 152 * 16);
+  k_cast_d2f<<<grid, kBlock, 0, L.s>>>(in, out, count);
+  L.bump();
+}
+
+}  // namespace pasm

@@ -1,0 +1,108 @@
+// Host-side launchers of the PASM device kernels (implemented in kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pasm {
+
+// Device CSR matrix with float64 values and an optional float32 shadow.
+struct DCsr {
+  int n_rows = 0, n_cols = 0;
+  int64_t nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+};
+
+template <typename T> inline const T* vals(const DCsr& m);
+template <> inline const double* vals<double>(const DCsr& m) { return m.v64; }
+template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
+
+// Launch bookkeeping shared by every launcher: the stream and a launch counter.
+struct Launch {
+  cudaStream_t s = nullptr;
+  int* counter = nullptr;
+  void bump() const { if (counter) ++*counter; }
+};
+
+enum RowOp { OP_JACOBI = 0, OP_RESID = 1, OP_SPMM = 2, OP_SPMM_ADD = 3 };
+
+// out = op(S, X, Y, Z) row by row on n x ldk block vectors (row-major):
+//   OP_JACOBI : out = Z + omega * dinv .* (Y - S X)      (damped Jacobi sweep)
+//   OP_RESID  : out = Y - S X                            (residual)
+//   OP_SPMM   : out = S X                                (restriction / product)
+//   OP_SPMM_ADD: out = Y + S X                           (prolongate and correct)
+template <typename T>
+void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, const T* Z, const T* dinv,
+           T omega, T* out, int ldk);
+
+// out = omega * dinv .* F  (first Jacobi sweep from a zero guess)
+template <typename T>
+void jacobi_zero(const Launch& L, int n, const T* dinv, T omega, const T* F, T* out, int ldk);
+
+// Fd = lam .* (M U)  and  R = Fd - A U  (float64 arithmetic, R stored as TV)
+template <typename TV>
+void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
+                        double* Fd, TV* R, int ldk);
+// R = Fd - A X  (float64 arithmetic, stored as TV)
+template <typename TV>
+void outer_residual(const Launch& L, const DCsr& A, const double* Fd, const double* X, TV* R, int ldk);
+// X = B + E (float64 result; X may alias B)
+template <typename TV>
+void outer_axpy(const Launch& L, int n, const double* B, const TV* E, double* X, int ldk);
+
+// YA = A X, YM = M X and per-column partial sums of X.*YA, X.*YM into
+// partials[nblk][2][ldk]; returns the number of blocks used.
+int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
+                    double* partials, int ldk, int max_blocks);
+// out[q*ldk + c] = sum_b partials[(b*nq + q)*ldk + c]
+void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out);
+
+// C (m x ldk) = op(D) (m x p) * B (p x ldk); D row-major with leading dim ldd;
+// trans: op(D) = D^T (then D is p x m).
+template <typename T>
+void dense_mm(const Launch& L, int m, int p, const T* D, int ldd, bool trans, const T* B, T* C, int ldk);
+
+// Coarse initial state: W0[j][c] = Q[j][c] / sqrt(lamH[c]) for c < k, 0 otherwise;
+// lam[c] = lamH[c] (c < k).
+void coarse_init(const Launch& L, int NH, int k, const double* Q, const double* lamH, double* W0, double* lam,
+                 int ldk);
+
+struct SecularArgs {
+  int NH, k, ldk;
+  const double* lamH;     // NH, ascending
+  const double* bq;       // NH x ldk: Q^T b
+  const double* cq;       // NH x ldk: Q^T c
+  const double* beta;     // ldk
+  const double* zeta;     // ldk
+  double* lam;            // ldk: in = lambda^(l), out = lambda^(l+1)
+  double* alpha;          // ldk out
+  double* g;              // NH x ldk out: coarse coefficients in the Q basis
+  int* active;            // ldk in/out
+  int* upd;               // ldk out: 1 = pair updated this step
+  int* steps;             // ldk in/out
+  int* status;            // ldk out
+  double tol;
+  int score_norm;
+  int window;             // half-width of the first root window
+  int* diag;              // diagnostics: [0] = roots solved, [1] = full solves, [2] = iteration caps hit
+};
+void secular_select(const Launch& L, const SecularArgs& a);
+// Raise the kernel's dynamic shared memory limit for a coarse dimension NH (once per setup).
+cudaError_t secular_prepare(int NH);
+
+// U[row][c] = upd[c] ? alpha[c] * X[row][c] + (P W)[row][c] : U[row][c]
+void update_pairs(const Launch& L, const DCsr& P, const double* W, const double* X, const double* alpha,
+                  const int* upd, double* U, int ldk);
+// Same with P = identity (single-level hierarchy): U = alpha X + W.
+void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
+                           const int* upd, double* U, int ldk);
+
+// *out = number of nonzero entries of active[0..k)
+void count_active(const Launch& L, const int* active, int k, int* out);
+
+// cast between float64 and float32 block vectors
+void cast_d2f(const Launch& L, const double* in, float* out, int64_t count);
+
+}  // namespace pasm

@@ -1,0 +1,679 @@
+// C ABI of the GB300 parallel augmented subspace method: context, setup,
+// correction step (Algorithm 1 for all pairs at once), solve loop
+// (Algorithm 2 on the finest level) and the split entry points.
+#include "../../include/pasm.h"
+#include "kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace pasm {
+int coarse_generalized_eig(int n, const double* A, const double* M, double* lam, double* Q);
+}
+using namespace pasm;
+
+namespace {
+
+struct LevelDev {
+  int n = 0;
+  DCsr A, M;       // level stiffness and mass
+  DCsr P, R;       // (l >= 1) P: level l-1 -> l, R = P^T
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  void* vF = nullptr;  // V-cycle right-hand side (precision of the cycle)
+  void* vE = nullptr;  // V-cycle iterate
+  void* vT = nullptr;  // V-cycle temporary
+  double* BA = nullptr;  // float64 chain buffers (restriction of A u~, prolongation of u_H)
+  double* BM = nullptr;  // float64 chain buffer (restriction of M u~)
+};
+
+}  // namespace
+
+struct pasm_ctx {
+  int nlev = 0;
+  std::vector<LevelDev> lv;
+  pasm_opts opts{};
+  cudaStream_t s = nullptr;
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int NH = 0;
+  std::vector<double> h_lamH, h_Q;
+  double* lamH = nullptr;
+  double* Q = nullptr;
+  double* AinvH64 = nullptr;
+  float* AinvH32 = nullptr;
+  std::vector<void*> allocs;     // setup-lifetime device allocations
+  std::vector<void*> kallocs;    // k-dependent device allocations
+  // pair state (k-dependent)
+  int k = 0, ldk = 0;
+  double tol = 0.0;
+  double *U = nullptr, *Fd = nullptr, *X = nullptr, *YA = nullptr, *YM = nullptr;
+  double *lam = nullptr, *lam2 = nullptr, *alpha = nullptr, *bz = nullptr, *bq = nullptr, *cq = nullptr,
+         *g = nullptr, *uH = nullptr, *partials = nullptr;
+  int *active = nullptr, *upd = nullptr, *steps = nullptr, *status = nullptr, *nact = nullptr, *diag = nullptr;
+  int *active2 = nullptr, *steps2 = nullptr, *status2 = nullptr;
+  int* h_nact = nullptr;  // pinned
+  int max_border_blocks = 152 * 8;
+  cudaGraphExec_t graph = nullptr;
+  int launches = 0;
+  int last_launches = 0;
+  bool initialized = false;
+};
+
+namespace {
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) {                                  \
+      std::fprintf(stderr, "pasm: %s failed: %s (%s:%d)\n", #call, cudaGetErrorString(_e), __FILE__, __LINE__); \
+      return PASM_ECUDA;                                      \
+    }                                                         \
+  } while (0)
+
+template <typename T>
+int dalloc(std::vector<void*>& list, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) { cudaGetLastError(); return PASM_ENOMEM; }
+  list.push_back(*p);
+  return PASM_OK;
+}
+#define AL(list, p, count) do { int _r = dalloc(list, p, count); if (_r) return _r; } while (0)
+
+int check_csr(const pasm_csr& m, int rows, int cols) {
+  if (m.n_rows != rows || m.n_cols != cols || m.nnz < 0 || !m.row_ptr) return PASM_EINVAL;
+  if (m.nnz > 0 && (!m.col || !m.val)) return PASM_EINVAL;
+  if (m.nnz > 2147483647LL) return PASM_EINVAL;
+  if (m.row_ptr[0] != 0 || m.row_ptr[rows] != m.nnz) return PASM_EINVAL;
+  for (int i = 0; i < rows; ++i)
+    if (m.row_ptr[i + 1] < m.row_ptr[i]) return PASM_EINVAL;
+  for (int64_t p = 0; p < m.nnz; ++p)
+    if (m.col[p] < 0 || m.col[p] >= cols) return PASM_EINVAL;
+  return PASM_OK;
+}
+
+int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32) {
+  d.n_rows = h.n_rows; d.n_cols = h.n_cols; d.nnz = h.nnz;
+  AL(c->allocs, &d.rp, (size_t)h.n_rows + 1);
+  AL(c->allocs, &d.ci, (size_t)h.nnz);
+  AL(c->allocs, &d.v64, (size_t)h.nnz);
+  CK(cudaMemcpy(d.rp, h.row_ptr, sizeof(int) * ((size_t)h.n_rows + 1), cudaMemcpyHostToDevice));
+  if (h.nnz) {
+    CK(cudaMemcpy(d.ci, h.col, sizeof(int) * (size_t)h.nnz, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d.v64, h.val, sizeof(double) * (size_t)h.nnz, cudaMemcpyHostToDevice));
+  }
+  if (shadow32) {
+    AL(c->allocs, &d.v32, (size_t)h.nnz);
+    std::vector<float> f(h.val, h.val + h.nnz);
+    if (h.nnz) CK(cudaMemcpy(d.v32, f.data(), sizeof(float) * (size_t)h.nnz, cudaMemcpyHostToDevice));
+  }
+  return PASM_OK;
+}
+
+// Host CSR transpose (R = P^T), columns ascending.
+void transpose_csr(const pasm_csr& p, std::vector<int32_t>& rp, std::vector<int32_t>& ci, std::vector<double>& v) {
+  rp.assign((size_t)p.n_cols + 1, 0);
+  for (int64_t q = 0; q < p.nnz; ++q) rp[(size_t)p.col[q] + 1]++;
+  for (int j = 0; j < p.n_cols; ++j) rp[(size_t)j + 1] += rp[j];
+  ci.resize((size_t)p.nnz);
+  v.resize((size_t)p.nnz);
+  std::vector<int32_t> pos(rp.begin(), rp.end() - 1);
+  for (int i = 0; i < p.n_rows; ++i)
+    for (int q = p.row_ptr[i]; q < p.row_ptr[i + 1]; ++q) {
+      const int j = p.col[q];
+      ci[(size_t)pos[j]] = i;
+      v[(size_t)pos[j]] = p.val[q];
+      pos[j]++;
+    }
+}
+
+int ldk_for(int k) {
+  int l = 4;
+  while (l < k) l <<= 1;
+  return l;
+}
+
+struct Scope {  // order the context stream after the caller's stream and back
+  pasm_ctx* c;
+  explicit Scope(pasm_ctx* ctx) : c(ctx) {
+    cudaEventRecord(c->ev_in, c->user);
+    cudaStreamWaitEvent(c->s, c->ev_in, 0);
+  }
+  ~Scope() {
+    cudaEventRecord(c->ev_out, c->s);
+    cudaStreamWaitEvent(c->user, c->ev_out, 0);
+  }
+};
+
+Launch launcher(pasm_ctx* c) {
+  Launch L;
+  L.s = c->s;
+  L.counter = &c->launches;
+  return L;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Multigrid V-cycle for A_l E = F_l from a zero guess; returns the buffer holding E.
+template <typename T> const T* ainv(pasm_ctx* c);
+template <> const double* ainv<double>(pasm_ctx* c) { return c->AinvH64; }
+template <> const float* ainv<float>(pasm_ctx* c) { return c->AinvH32; }
+template <typename T> const T* dinv(const LevelDev& v);
+template <> const double* dinv<double>(const LevelDev& v) { return v.dinv64; }
+template <> const float* dinv<float>(const LevelDev& v) { return v.dinv32; }
+
+template <typename T>
+T* vcycle(pasm_ctx* c, int l) {
+  const Launch L = launcher(c);
+  LevelDev& v = c->lv[l];
+  T* F = (T*)v.vF;
+  T* E = (T*)v.vE;
+  T* Tm = (T*)v.vT;
+  const int ldk = c->ldk;
+  if (l == 0) {
+    dense_mm<T>(L, c->NH, c->NH, ainv<T>(c), c->NH, false, F, E, ldk);
+    return E;
+  }
+  const T om = (T)c->opts.omega;
+  T* cur = E;
+  T* tmp = Tm;
+  if (c->opts.nu_pre >= 1) {
+    jacobi_zero<T>(L, v.n, dinv<T>(v), om, F, cur, ldk);
+  } else {
+    cudaMemsetAsync(cur, 0, sizeof(T) * (size_t)v.n * ldk, c->s);
+  }
+  for (int s = 1; s < c->opts.nu_pre; ++s) {
+    rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
+    std::swap(cur, tmp);
+  }
+  rowop<T>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
+  rowop<T>(L, OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om, (T*)c->lv[l - 1].vF, ldk);
+  T* ec = vcycle<T>(c, l - 1);
+  rowop<T>(L, OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
+  for (int s = 0; s < c->opts.nu_post; ++s) {
+    rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
+    std::swap(cur, tmp);
+  }
+  return cur;
+}
+
+// Algorithm 1 step 1 on level lt: X = result of the V-cycles for A x = lam M U from x = U,
+// each cycle a defect correction x += V(f - A x) with f = lam M U (float64 residual).
+template <typename T>
+void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X) {
+  const Launch L = launcher(c);
+  LevelDev& v = c->lv[lt];
+  T* Ftop = (T*)v.vF;
+  outer_rhs_residual<T>(L, v.A, v.M, lam, U, c->Fd, Ftop, c->ldk);
+  T* e = vcycle<T>(c, lt);
+  outer_axpy<T>(L, v.n, U, e, X, c->ldk);
+  for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
+    outer_residual<T>(L, v.A, c->Fd, X, Ftop, c->ldk);
+    e = vcycle<T>(c, lt);
+    outer_axpy<T>(L, v.n, X, e, X, c->ldk);
+  }
+}
+
+void bvp(pasm_ctx* c, int lt, const double* lam, const double* U, double* X) {
+  if (c->opts.precision == PASM_MIXED) bvp_impl<float>(c, lt, lam, U, X);
+  else bvp_impl<double>(c, lt, lam, U, X);
+}
+
+struct PairState {
+  double* lam;
+  int* active;
+  int* steps;
+  int* status;
+  double* Uout;
+  double tol;
+};
+
+// Algorithm 1 step 2 on level lt for the columns of X: bordering, projection,
+// secular solve and selection, and the update Uout = alpha X + P_c u_H.
+void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
+  const Launch L = launcher(c);
+  LevelDev& v = c->lv[lt];
+  const int ldk = c->ldk;
+  const int nb = border_products(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
+  column_sums(L, c->partials, nb, 2, ldk, c->bz);
+  const double* sa = c->YA;
+  const double* sm = c->YM;
+  for (int l = lt; l >= 1; --l) {
+    rowop<double>(L, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
+    rowop<double>(L, OP_SPMM, c->lv[l].R, sm, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BM, ldk);
+    sa = c->lv[l - 1].BA;
+    sm = c->lv[l - 1].BM;
+  }
+  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, sa, c->bq, ldk);
+  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, sm, c->cq, ldk);
+  SecularArgs a;
+  a.NH = c->NH; a.k = c->k; a.ldk = ldk;
+  a.lamH = c->lamH; a.bq = c->bq; a.cq = c->cq;
+  a.beta = c->bz; a.zeta = c->bz + ldk;
+  a.lam = ps.lam; a.alpha = c->alpha; a.g = c->g;
+  a.active = ps.active; a.upd = c->upd; a.steps = ps.steps; a.status = ps.status;
+  a.tol = ps.tol; a.score_norm = c->opts.score_norm; a.window = 3; a.diag = c->diag;
+  secular_select(L, a);
+  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, false, c->g, c->uH, ldk);
+  const double* w = c->uH;
+  for (int l = 1; l < lt; ++l) {
+    rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
+    w = c->lv[l].BA;
+  }
+  if (lt >= 1) update_pairs(L, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
+  else update_pairs_identity(L, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
+}
+
+// One correction step for all active pairs on the finest level.
+void step_body(pasm_ctx* c) {
+  const int lt = c->nlev - 1;
+  bvp(c, lt, c->lam, c->U, c->X);
+  PairState ps{c->lam, c->active, c->steps, c->status, c->U, c->tol};
+  augmented(c, lt, c->X, ps);
+  count_active(launcher(c), c->active, c->k, c->nact);
+  cudaMemcpyAsync(c->h_nact, c->nact, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+}
+
+void free_k(pasm_ctx* c) {
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  for (void* p : c->kallocs) cudaFree(p);
+  c->kallocs.clear();
+  for (auto& v : c->lv) { v.vF = v.vE = v.vT = nullptr; v.BA = v.BM = nullptr; }
+  c->initialized = false;
+  c->k = 0;
+}
+
+int alloc_k(pasm_ctx* c, int k) {
+  free_k(c);
+  c->k = k;
+  c->ldk = ldk_for(k);
+  const size_t ldk = (size_t)c->ldk;
+  const size_t n = (size_t)c->lv.back().n;
+  const bool mixed = c->opts.precision == PASM_MIXED;
+  auto& K = c->kallocs;
+  AL(K, &c->U, n * ldk); AL(K, &c->Fd, n * ldk); AL(K, &c->X, n * ldk);
+  AL(K, &c->YA, n * ldk); AL(K, &c->YM, n * ldk);
+  for (int l = 0; l < c->nlev; ++l) {
+    LevelDev& v = c->lv[l];
+    const size_t m = (size_t)v.n * ldk;
+    if (mixed) {
+      float *a, *b, *t;
+      AL(K, &a, m); AL(K, &b, m); AL(K, &t, m);
+      v.vF = a; v.vE = b; v.vT = t;
+    } else {
+      double *a, *b, *t;
+      AL(K, &a, m); AL(K, &b, m); AL(K, &t, m);
+      v.vF = a; v.vE = b; v.vT = t;
+    }
+    if (l < c->nlev - 1) { AL(K, &v.BA, m); AL(K, &v.BM, m); }
+  }
+  const size_t nh = (size_t)c->NH * ldk;
+  AL(K, &c->lam, ldk); AL(K, &c->lam2, ldk); AL(K, &c->alpha, ldk); AL(K, &c->bz, 2 * ldk);
+  AL(K, &c->bq, nh); AL(K, &c->cq, nh); AL(K, &c->g, nh); AL(K, &c->uH, nh);
+  AL(K, &c->partials, (size_t)c->max_border_blocks * 2 * ldk);
+  AL(K, &c->active, ldk); AL(K, &c->upd, ldk); AL(K, &c->steps, ldk); AL(K, &c->status, ldk);
+  AL(K, &c->active2, ldk); AL(K, &c->steps2, ldk); AL(K, &c->status2, ldk);
+  AL(K, &c->nact, 1); AL(K, &c->diag, 8);
+  CK(cudaMemsetAsync(c->U, 0, sizeof(double) * n * ldk, c->s));
+  CK(cudaMemsetAsync(c->X, 0, sizeof(double) * n * ldk, c->s));
+  CK(cudaMemsetAsync(c->diag, 0, sizeof(int) * 8, c->s));
+  return PASM_OK;
+}
+
+int set_active(pasm_ctx* c, int* active, int* steps, int* status) {
+  std::vector<int> h((size_t)c->ldk, 0);
+  for (int i = 0; i < c->k; ++i) h[(size_t)i] = 1;
+  CK(cudaMemcpyAsync(active, h.data(), sizeof(int) * c->ldk, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemsetAsync(steps, 0, sizeof(int) * c->ldk, c->s));
+  CK(cudaMemsetAsync(status, 0, sizeof(int) * c->ldk, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+// Copy an n x k user block (host or device, leading dim k) into an n x ldk device block.
+int put_block(pasm_ctx* c, const double* src, double* dst, int n) {
+  CK(cudaMemsetAsync(dst, 0, sizeof(double) * (size_t)n * c->ldk, c->s));
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * c->ldk, src, sizeof(double) * c->k, sizeof(double) * c->k, n,
+                       cudaMemcpyDefault, c->s));
+  return PASM_OK;
+}
+int get_block(pasm_ctx* c, const double* src, double* dst, int n) {
+  CK(cudaMemcpy2DAsync(dst, sizeof(double) * c->k, src, sizeof(double) * c->ldk, sizeof(double) * c->k, n,
+                       cudaMemcpyDefault, c->s));
+  return PASM_OK;
+}
+int put_lambda(pasm_ctx* c, const double* src, double* dst) {
+  std::vector<double> ones((size_t)c->ldk, 1.0);
+  CK(cudaMemcpyAsync(dst, ones.data(), sizeof(double) * c->ldk, cudaMemcpyHostToDevice, c->s));
+  CK(cudaMemcpyAsync(dst, src, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+void pasm_default_opts(pasm_opts* o) {
+  if (!o) return;
+  o->omega = 2.0 / 3.0;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->cycles_per_step = 2;
+  o->max_steps = 100;
+  o->precision = PASM_FP64;
+  o->score_norm = PASM_SCORE_A;
+  o->init = PASM_INIT_COARSE;
+  o->use_graph = 1;
+}
+
+const char* pasm_strerror(int st) {
+  switch (st) {
+    case PASM_OK: return "success";
+    case PASM_EINVAL: return "invalid argument (malformed CSR, shape mismatch or bad option)";
+    case PASM_EK_TOO_BIG: return "k exceeds the coarse space dimension";
+    case PASM_ENOMEM: return "out of memory";
+    case PASM_ECUDA: return "CUDA runtime error";
+    case PASM_ENOTCONV: return "max_steps reached with pairs still active";
+    case PASM_EDEGENERATE: return "bordered mass matrix singular for a pair";
+    case PASM_ENAN: return "NaN or Inf in a pair";
+    case PASM_ESTATE: return "call out of order";
+    case PASM_ENOTPD: return "coarse matrix not symmetric positive definite";
+    default: return "unknown status";
+  }
+}
+
+void pasm_destroy(pasm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->s);
+  free_k(c);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_nact) cudaFreeHost(c->h_nact);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->s) cudaStreamDestroy(c->s);
+  delete c;
+}
+
+// Host-only validation of the hierarchy (no CUDA call): shapes, CSR structure,
+// positive diagonal of every A_l (needed by the Jacobi smoother), coarse size.
+static int validate_levels(int n_levels, const pasm_csr* A, const pasm_csr* M, const pasm_csr* P) {
+  for (int l = 0; l < n_levels; ++l) {
+    const int n = A[l].n_rows;
+    if (n < 1) return PASM_EINVAL;
+    int r = check_csr(A[l], n, n);
+    if (!r) r = check_csr(M[l], n, n);
+    if (l >= 1 && !r) r = check_csr(P[l - 1], n, A[l - 1].n_rows);
+    if (r) return r;
+    for (int i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int q = A[l].row_ptr[i]; q < A[l].row_ptr[i + 1]; ++q)
+        if (A[l].col[q] == i) d += A[l].val[q];
+      if (!(d > 0.0)) return PASM_EINVAL;
+    }
+  }
+  if (A[0].n_rows > 1024) return PASM_EINVAL;
+  return PASM_OK;
+}
+
+static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_csr* M, const pasm_csr* P) {
+  c->nlev = n_levels;
+  c->lv.resize((size_t)n_levels);
+  const bool mixed = c->opts.precision == PASM_MIXED;
+  for (int l = 0; l < n_levels; ++l) c->lv[(size_t)l].n = A[l].n_rows;
+  for (int l = 0; l < n_levels; ++l) {
+    LevelDev& v = c->lv[(size_t)l];
+    int r = upload_csr(c, A[l], v.A, mixed);
+    if (!r) r = upload_csr(c, M[l], v.M, false);
+    if (r) return r;
+    std::vector<double> d((size_t)v.n, 0.0);
+    for (int i = 0; i < v.n; ++i)
+      for (int q = A[l].row_ptr[i]; q < A[l].row_ptr[i + 1]; ++q)
+        if (A[l].col[q] == i) d[(size_t)i] = A[l].val[q];
+    std::vector<double> di((size_t)v.n);
+    std::vector<float> df((size_t)v.n);
+    for (int i = 0; i < v.n; ++i) {
+      if (!(d[(size_t)i] > 0.0)) return PASM_EINVAL;
+      di[(size_t)i] = 1.0 / d[(size_t)i];
+      df[(size_t)i] = (float)di[(size_t)i];
+    }
+    AL(c->allocs, &v.dinv64, (size_t)v.n);
+    CK(cudaMemcpy(v.dinv64, di.data(), sizeof(double) * v.n, cudaMemcpyHostToDevice));
+    if (mixed) {
+      AL(c->allocs, &v.dinv32, (size_t)v.n);
+      CK(cudaMemcpy(v.dinv32, df.data(), sizeof(float) * v.n, cudaMemcpyHostToDevice));
+    }
+    if (l >= 1) {
+      const pasm_csr& p = P[l - 1];
+      r = upload_csr(c, p, v.P, mixed);
+      if (r) return r;
+      std::vector<int32_t> rp, ci;
+      std::vector<double> rv;
+      transpose_csr(p, rp, ci, rv);
+      pasm_csr rt{p.n_cols, p.n_rows, p.nnz, rp.data(), ci.data(), rv.data()};
+      r = upload_csr(c, rt, v.R, mixed);
+      if (r) return r;
+    }
+  }
+  // coarse pencil: dense A_H, M_H -> Lambda_H, Q (Algorithm 2 step 1 on V_H)
+  const int NH = c->lv[0].n;
+  c->NH = NH;
+  std::vector<double> Ad((size_t)NH * NH, 0.0), Md((size_t)NH * NH, 0.0);
+  for (int i = 0; i < NH; ++i) {
+    for (int q = A[0].row_ptr[i]; q < A[0].row_ptr[i + 1]; ++q) Ad[(size_t)i * NH + A[0].col[q]] += A[0].val[q];
+    for (int q = M[0].row_ptr[i]; q < M[0].row_ptr[i + 1]; ++q) Md[(size_t)i * NH + M[0].col[q]] += M[0].val[q];
+  }
+  c->h_lamH.assign((size_t)NH, 0.0);
+  c->h_Q.assign((size_t)NH * NH, 0.0);
+  if (coarse_generalized_eig(NH, Ad.data(), Md.data(), c->h_lamH.data(), c->h_Q.data())) return PASM_ENOTPD;
+  // A_H^{-1} = Q Lambda^{-1} Q^T for the exact coarsest solve of the V-cycle
+  std::vector<double> Ai((size_t)NH * NH, 0.0);
+  for (int i = 0; i < NH; ++i)
+    for (int j = 0; j < NH; ++j) {
+      double s = 0.0;
+      for (int p = 0; p < NH; ++p) s += c->h_Q[(size_t)i * NH + p] * c->h_Q[(size_t)j * NH + p] / c->h_lamH[(size_t)p];
+      Ai[(size_t)i * NH + j] = s;
+    }
+  CK(secular_prepare(NH));
+  AL(c->allocs, &c->lamH, (size_t)NH);
+  AL(c->allocs, &c->Q, (size_t)NH * NH);
+  AL(c->allocs, &c->AinvH64, (size_t)NH * NH);
+  CK(cudaMemcpy(c->lamH, c->h_lamH.data(), sizeof(double) * NH, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->Q, c->h_Q.data(), sizeof(double) * NH * NH, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->AinvH64, Ai.data(), sizeof(double) * NH * NH, cudaMemcpyHostToDevice));
+  if (mixed) {
+    std::vector<float> af(Ai.begin(), Ai.end());
+    AL(c->allocs, &c->AinvH32, (size_t)NH * NH);
+    CK(cudaMemcpy(c->AinvH32, af.data(), sizeof(float) * NH * NH, cudaMemcpyHostToDevice));
+  }
+  return PASM_OK;
+}
+
+int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* M, const pasm_csr* P,
+               const pasm_opts* opts, void* stream) {
+  if (!out) return PASM_EINVAL;
+  *out = nullptr;
+  if (n_levels < 1 || !A || !M || (n_levels > 1 && !P)) return PASM_EINVAL;
+  pasm_opts o;
+  pasm_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.nu_pre < 0 || o.nu_post < 0 || o.cycles_per_step < 1 || o.max_steps < 0 || !(o.omega > 0.0) ||
+      (o.precision != PASM_FP64 && o.precision != PASM_MIXED) ||
+      (o.score_norm != PASM_SCORE_A && o.score_norm != PASM_SCORE_B) ||
+      (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED))
+    return PASM_EINVAL;
+  int v = validate_levels(n_levels, A, M, P);
+  if (v) return v;
+  pasm_ctx* c = new (std::nothrow) pasm_ctx();
+  if (!c) return PASM_ENOMEM;
+  c->opts = o;
+  c->user = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost((void**)&c->h_nact, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    pasm_destroy(c);
+    return PASM_ECUDA;
+  }
+  int r = setup_impl(c, n_levels, A, M, P);
+  if (r) { pasm_destroy(c); return r; }
+  *out = c;
+  return PASM_OK;
+}
+
+int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0) {
+  if (!c || k < 1 || k > 256 || !(tol >= 0.0)) return PASM_EINVAL;
+  if ((lambda0 == nullptr) != (U0 == nullptr)) return PASM_EINVAL;
+  if (!lambda0 && k > c->NH) return PASM_EK_TOO_BIG;
+  Scope sc(c);
+  int r = alloc_k(c, k);
+  if (r) return r;
+  c->tol = tol;
+  const int nf = c->lv.back().n;
+  const Launch L = launcher(c);
+  if (lambda0) {
+    r = put_lambda(c, lambda0, c->lam);
+    if (!r) r = put_block(c, U0, c->U, nf);
+    if (r) return r;
+  } else {
+    // u_i = P_c q_i / sqrt(Lambda_i), lambda_i = Lambda_i
+    double* w = (c->nlev == 1) ? c->U : c->uH;
+    coarse_init(L, c->NH, k, c->Q, c->lamH, w, c->lam, c->ldk);
+    for (int l = 1; l < c->nlev; ++l) {
+      double* dst = (l == c->nlev - 1) ? c->U : c->lv[l].BA;
+      rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, dst, c->ldk);
+      w = dst;
+    }
+  }
+  r = set_active(c, c->active, c->steps, c->status);
+  if (r) return r;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  c->initialized = true;
+  return PASM_OK;
+}
+
+int pasm_step(pasm_ctx* c, int* n_active) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  Scope sc(c);
+  if (c->opts.use_graph) {
+    if (!c->graph) {
+      cudaGraph_t g;
+      c->launches = 0;
+      CK(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+      step_body(c);
+      CK(cudaStreamEndCapture(c->s, &g));
+      cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      c->last_launches = c->launches;
+    }
+    CK(cudaGraphLaunch(c->graph, c->s));
+  } else {
+    c->launches = 0;
+    step_body(c);
+    c->last_launches = c->launches;
+    CK(cudaGetLastError());
+  }
+  if (n_active) {
+    CK(cudaStreamSynchronize(c->s));
+    *n_active = *c->h_nact;
+  }
+  return PASM_OK;
+}
+
+int pasm_get(pasm_ctx* c, double* lambda, double* U, int* steps, int* status) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  Scope sc(c);
+  if (lambda) CK(cudaMemcpyAsync(lambda, c->lam, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
+  if (U) { int r = get_block(c, c->U, U, c->lv.back().n); if (r) return r; }
+  if (steps) CK(cudaMemcpyAsync(steps, c->steps, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
+  if (status) CK(cudaMemcpyAsync(status, c->status, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_solve(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0, double* lambda_out,
+               double* U_out, int* steps_out, int* status_out) {
+  if (!c) return PASM_EINVAL;
+  int r = pasm_init(c, k, tol, lambda0, U0);
+  if (r) return r;
+  int act = k;
+  for (int s = 0; s < c->opts.max_steps && act > 0; ++s) {
+    r = pasm_step(c, &act);
+    if (r) return r;
+  }
+  r = pasm_get(c, lambda_out, U_out, steps_out, status_out);
+  if (r) return r;
+  return act > 0 ? PASM_ENOTCONV : PASM_OK;
+}
+
+int pasm_bvp(pasm_ctx* c, const double* lambda, const double* U, double* Uhat) {
+  if (!c || !c->initialized || !lambda || !U || !Uhat) return PASM_ESTATE;
+  Scope sc(c);
+  const int nf = c->lv.back().n;
+  int r = put_lambda(c, lambda, c->lam2);
+  if (!r) r = put_block(c, U, c->YM, nf);
+  if (r) return r;
+  bvp(c, c->nlev - 1, c->lam2, c->YM, c->X);
+  CK(cudaGetLastError());
+  r = get_block(c, c->X, Uhat, nf);
+  if (r) return r;
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, double* lambda_out, double* U_out,
+                   double* beta, double* zeta) {
+  if (!c || !c->initialized || !lambda_prev || !Uhat) return PASM_ESTATE;
+  Scope sc(c);
+  const int nf = c->lv.back().n;
+  int r = put_lambda(c, lambda_prev, c->lam2);
+  if (!r) r = put_block(c, Uhat, c->X, nf);
+  if (!r) r = set_active(c, c->active2, c->steps2, c->status2);
+  if (r) return r;
+  CK(cudaMemcpyAsync(c->Fd, c->X, sizeof(double) * (size_t)nf * c->ldk, cudaMemcpyDeviceToDevice, c->s));
+  PairState ps{c->lam2, c->active2, c->steps2, c->status2, c->Fd, 0.0};
+  augmented(c, c->nlev - 1, c->X, ps);
+  CK(cudaGetLastError());
+  if (lambda_out) CK(cudaMemcpyAsync(lambda_out, c->lam2, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
+  if (U_out) { r = get_block(c, c->Fd, U_out, nf); if (r) return r; }
+  if (beta) CK(cudaMemcpyAsync(beta, c->bz, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
+  if (zeta) CK(cudaMemcpyAsync(zeta, c->bz + c->ldk, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_coarse_eigs(pasm_ctx* c, double* lambda_H, double* Q) {
+  if (!c) return PASM_EINVAL;
+  if (lambda_H) std::memcpy(lambda_H, c->h_lamH.data(), sizeof(double) * c->NH);
+  if (Q) std::memcpy(Q, c->h_Q.data(), sizeof(double) * (size_t)c->NH * c->NH);
+  return PASM_OK;
+}
+
+int pasm_sizes(pasm_ctx* c, int64_t* n_fine, int32_t* n_coarse, int32_t* n_levels, int32_t* k) {
+  if (!c) return PASM_EINVAL;
+  if (n_fine) *n_fine = c->lv.back().n;
+  if (n_coarse) *n_coarse = c->NH;
+  if (n_levels) *n_levels = c->nlev;
+  if (k) *k = c->k;
+  return PASM_OK;
+}
+
+int pasm_last_launches(pasm_ctx* c, int* launches) {
+  if (!c || !launches) return PASM_EINVAL;
+  *launches = c->last_launches;
+  return PASM_OK;
+}
+
+}  // extern "C"

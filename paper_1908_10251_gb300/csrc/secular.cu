@@ -1,0 +1,388 @@
+// Batched augmented eigensolve and selection (Algorithm 1 step 2) on sm_103a.
+//
+// For one pair the bordered pencil of Section 3.1,
+//     [[A_H, b], [b^T, beta]] x = theta [[M_H, c], [c^T, zeta]] x,
+// is reduced once per setup by the coarse eigendecomposition A_H Q = M_H Q Lambda
+// (Q^T M_H Q = I).  In the b-orthonormal basis {P_c q_j} + {w^} with
+// w = u~ - P_c Q c',  c' = Q^T c,  b' = Q^T b,  zt = zeta - |c'|^2 = |w|_b^2,
+// the pencil becomes the symmetric arrowhead matrix [[Lambda, z], [z^T, rho]]:
+//     z   = (b' - Lambda c') / sqrt(zt),
+//     rho = (beta - 2 c'.b' + c'^T Lambda c') / zt.
+// Its eigenvalues are the roots of the secular equation
+//     f(theta) = theta - rho + sum_j z_j^2 / (lambda_j - theta) = 0,
+// one in each gap between consecutive poles (Cauchy interlacing), plus one
+// below and one above.  Eigenvector of root theta: [y; 1] with
+// y_j = -z_j / (lambda_j - theta).  Its component along u~ is
+// b(v, u~) = (y.c' + sqrt(zt)) / |[y; 1]|  (b-normalised); the a-normalised
+// score divides by sqrt(theta).  Since u~ lies in V_{H,h}, the squared
+// b-normalised scores of all roots sum to zeta (Parseval), which certifies the
+// winner from a window of roots around the current eigenvalue.
+//
+// Root finder: safeguarded rational interpolation in the spirit of Bunch,
+// Nielsen and Sorensen (1978) -- the left and right partial sums are modelled
+// by one pole each (the linear term joins the right part), matching value and
+// derivative at the iterate, and the model's root in the interval is taken;
+// steps leaving the bracket fall back to bisection.  The iterate is kept as an
+// offset tau from the nearer pole so that lambda_j - theta is formed without
+// cancellation.  Indices with |z_j| below 8 eps times the problem scale are
+// deflated: theta = lambda_j with eigenvector e_j.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <cfloat>
+
+namespace pasm {
+
+static constexpr int kSecThreads = 256;
+static constexpr int kSecWarps = kSecThreads / 32;
+static constexpr int kMaxIter = 80;
+
+enum { ST_ACTIVE = 0, ST_CONVERGED = 1, ST_DEGENERATE = 2, ST_NAN = 3 };
+
+struct SecShared {
+  double* d;      // NH
+  double* z;      // NH
+  double* cq;     // NH
+  int* J;         // NH: non-deflated indices, ascending
+  double* theta;  // NH+1 roots
+  double* orig;   // NH+1 origin (pole) of each root
+  double* tau;    // NH+1 offset from origin
+  double* sb;     // NH+1 signed b-normalised score
+  int* solved;    // NH+1
+};
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < kSecWarps) ? red[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Sums over the non-deflated poles at theta = origin + tau, split into the
+// poles left of root m (indices t < m) and right of it.  Warp-cooperative.
+__device__ __forceinline__ void secular_sums(const SecShared& S, int nJ, int m, double origin, double tau, int lane,
+                                             double& psi, double& dpsi, double& phi, double& dphi) {
+  psi = dpsi = phi = dphi = 0.0;
+  for (int t = lane; t < nJ; t += 32) {
+    const int j = S.J[t];
+    const double del = (S.d[j] - origin) - tau;
+    const double q = S.z[j] / del;
+    const double term = S.z[j] * q;
+    const double dterm = q * q;
+    if (t < m) { psi += term; dpsi += dterm; }
+    else { phi += term; dphi += dterm; }
+  }
+  psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
+}
+
+// Root m of the secular equation (0 <= m <= nJ), computed by one warp.
+__device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double lower, double upper, int lane,
+                           int* caps) {
+  const bool has_left = m > 0, has_right = m < nJ;
+  if (!has_left && !has_right) {  // every pole deflated: the bordered row alone, theta = rho
+    if (lane == 0) { S.theta[m] = rho; S.orig[m] = rho; S.tau[m] = 0.0; }
+    __syncwarp();
+    return;
+  }
+  const double a = has_left ? S.d[S.J[m - 1]] : lower;
+  const double b = has_right ? S.d[S.J[m]] : upper;
+  double origin, lo, hi;
+  if (!has_left) { origin = b; lo = lower - b; hi = 0.0; }
+  else if (!has_right) { origin = a; lo = 0.0; hi = upper - a; }
+  else {
+    const double mid = 0.5 * (a + b);
+    double psi, dpsi, phi, dphi;
+    secular_sums(S, nJ, m, 0.0, mid, lane, psi, dpsi, phi, dphi);
+    const double fmid = mid - rho + psi + phi;
+    if (fmid >= 0.0) { origin = a; lo = 0.0; hi = mid - a; }
+    else { origin = b; lo = mid - b; hi = 0.0; }
+  }
+  double tau = 0.5 * (lo + hi);
+  int it = 0;
+  for (; it < kMaxIter; ++it) {
+    double psi, dpsi, phi, dphi;
+    secular_sums(S, nJ, m, origin, tau, lane, psi, dpsi, phi, dphi);
+    const double th = origin + tau;
+    const double f = th - rho + psi + phi;
+    const double eb = 16.0 * DBL_EPSILON * (fabs(th) + fabs(rho) + fabs(psi) + fabs(phi));
+    if (fabs(f) <= eb) break;
+    if (f > 0.0) hi = tau; else lo = tau;
+    if (hi - lo <= 4.0 * DBL_EPSILON * fabs(th)) break;
+    double s = 0.0;
+    bool ok = false;
+    if (has_left && has_right) {
+      const double da = (a - origin) - tau, db = (b - origin) - tau;  // a - theta < 0 < b - theta
+      const double Q1 = dpsi * da * da, P1 = psi - Q1 / da;
+      const double ft = th - rho + phi;
+      const double Q2 = (dphi + 1.0) * db * db, P2 = ft - Q2 / db;
+      const double P = P1 + P2;
+      const double A2 = P, B2 = -(P * (da + db) + Q1 + Q2), C2 = P * da * db + Q1 * db + Q2 * da;
+      const double disc = fmax(B2 * B2 - 4.0 * A2 * C2, 0.0);
+      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
+      const double s1 = (A2 != 0.0) ? q / A2 : 0.0, s2 = (q != 0.0) ? C2 / q : 0.0;
+      if (A2 != 0.0 && s1 > da && s1 < db) { s = s1; ok = true; }
+      if (q != 0.0 && s2 > da && s2 < db) { s = s2; ok = true; }
+    } else if (!has_left && has_right) {
+      const double db = (b - origin) - tau;
+      const double Q2 = dphi * db * db, P2 = phi - Q2 / db;
+      const double f0 = th - rho + P2;
+      const double B2 = -(db - f0), C2 = -(f0 * db + Q2);
+      const double disc = fmax(B2 * B2 - 4.0 * C2, 0.0);
+      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
+      const double s1 = q, s2 = (q != 0.0) ? C2 / q : 0.0;
+      const double sm = fmin(s1, s2);
+      if (sm < db) { s = sm; ok = true; }
+    } else if (has_left && !has_right) {
+      const double da = (a - origin) - tau;
+      const double Q1 = dpsi * da * da, P1 = psi - Q1 / da;
+      const double f0 = th - rho + P1;
+      const double B2 = -(da - f0), C2 = -(f0 * da + Q1);
+      const double disc = fmax(B2 * B2 - 4.0 * C2, 0.0);
+      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
+      const double s1 = q, s2 = (q != 0.0) ? C2 / q : 0.0;
+      const double sm = fmax(s1, s2);
+      if (sm > da) { s = sm; ok = true; }
+    }
+    double tn = tau + s;
+    if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
+    const bool tiny = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(origin + tn);
+    tau = tn;
+    if (tiny) break;
+  }
+  if (it == kMaxIter && lane == 0) atomicAdd(caps, 1);
+  if (lane == 0) {
+    S.theta[m] = origin + tau;
+    S.orig[m] = origin;
+    S.tau[m] = tau;
+  }
+  __syncwarp();
+}
+
+// Signed b-normalised score and |y|^2 of root m (warp-cooperative).
+__device__ __forceinline__ void root_vector_sums(const SecShared& S, int nJ, int m, int lane, double& ny2,
+                                                 double& yc) {
+  const double origin = S.orig[m], tau = S.tau[m];
+  ny2 = 0.0; yc = 0.0;
+  for (int t = lane; t < nJ; t += 32) {
+    const int j = S.J[t];
+    const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+    ny2 = fma(y, y, ny2);
+    yc = fma(y, S.cq[j], yc);
+  }
+  ny2 = warp_sum(ny2); yc = warp_sum(yc);
+}
+
+__global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
+  extern __shared__ double smem[];
+  __shared__ double red[32];
+  __shared__ int s_nJ, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
+  __shared__ double s_lower, s_upper;
+  const int i = blockIdx.x;
+  const int NH = a.NH, ldk = a.ldk;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (!a.active[i]) {
+    if (tid == 0) a.upd[i] = 0;
+    return;
+  }
+  SecShared S;
+  S.d = smem;
+  S.z = S.d + NH;
+  S.cq = S.z + NH;
+  S.theta = S.cq + NH;
+  S.orig = S.theta + NH + 1;
+  S.tau = S.orig + NH + 1;
+  S.sb = S.tau + NH + 1;
+  S.J = reinterpret_cast<int*>(S.sb + NH + 1);
+  S.solved = S.J + NH;
+
+  double scc = 0.0, scb = 0.0, sdcc = 0.0;
+  for (int j = tid; j < NH; j += kSecThreads) {
+    const double dj = a.lamH[j], cj = a.cq[(size_t)j * ldk + i], bj = a.bq[(size_t)j * ldk + i];
+    S.d[j] = dj; S.cq[j] = cj; S.z[j] = bj;  // z holds b' until rescaled
+    scc = fma(cj, cj, scc); scb = fma(cj, bj, scb); sdcc = fma(dj * cj, cj, sdcc);
+  }
+  scc = block_sum(scc, red); scb = block_sum(scb, red); sdcc = block_sum(sdcc, red);
+  const double beta = a.beta[i], zeta = a.zeta[i];
+  const double zt = zeta - scc;
+  if (!(zt > 1e-14 * zeta)) {  // u~ numerically inside V_H: keep the pair for this step
+    if (tid == 0) { a.upd[i] = 0; a.status[i] = ST_DEGENERATE; a.steps[i] += 1; }
+    return;
+  }
+  const double sq = sqrt(zt);
+  const double rho = (beta - 2.0 * scb + sdcc) / zt;
+  double zz = 0.0;
+  for (int j = tid; j < NH; j += kSecThreads) {
+    const double zj = (S.z[j] - S.d[j] * S.cq[j]) / sq;
+    S.z[j] = zj;
+    zz = fma(zj, zj, zz);
+  }
+  zz = block_sum(zz, red);
+  const double scale = fmax(fmax(fabs(S.d[NH - 1]), fabs(rho)), sqrt(zz));
+  const double tolz = 8.0 * DBL_EPSILON * scale;
+  const double lam_prev = a.lam[i];
+  if (tid == 0) {
+    int nJ = 0, m0 = 0;
+    double zj2 = 0.0, dmin = 0.0, dmax = 0.0;
+    for (int j = 0; j < NH; ++j) {
+      if (fabs(S.z[j]) > tolz) {
+        if (nJ == 0) dmin = S.d[j];
+        dmax = S.d[j];
+        S.J[nJ++] = j;
+        zj2 += S.z[j] * S.z[j];
+        if (S.d[j] < lam_prev) m0 = nJ;
+      }
+    }
+    const double zn = sqrt(zj2);
+    s_nJ = nJ;
+    s_lower = (nJ ? fmin(dmin, rho) : rho) - zn;
+    s_upper = (nJ ? fmax(dmax, rho) : rho) + zn;
+    // phase-1 list: root 0 and a window around the root holding lambda^(l)
+    int nl = 0;
+    s_list[nl++] = 0;
+    const int w = a.window;
+    for (int m = max(1, m0 - w); m <= min(nJ, m0 + w); ++m) s_list[nl++] = m;
+    if (nl == 1 && nJ == 0) nl = 1;
+    s_nlist = nl;
+    a.steps[i] += 1;
+  }
+  for (int m = tid; m <= NH; m += kSecThreads) S.solved[m] = 0;
+  __syncthreads();
+  const int nJ = s_nJ;
+  const double lower = s_lower, upper = s_upper;
+
+  for (int phase = 0; phase < 2; ++phase) {
+    // solve the listed roots (phase 0) or every remaining root (phase 1)
+    if (phase == 0) {
+      for (int q = warp; q < s_nlist; q += kSecWarps) {
+        const int m = s_list[q];
+        solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
+        double ny2, yc;
+        root_vector_sums(S, nJ, m, lane, ny2, yc);
+        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
+      }
+    } else {
+      for (int m = warp; m <= nJ; m += kSecWarps) {
+        if (S.solved[m]) continue;
+        solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
+        double ny2, yc;
+        root_vector_sums(S, nJ, m, lane, ny2, yc);
+        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // best candidate among solved roots and deflated poles
+      double best = -1.0, best_th = 0.0, mass = 0.0;
+      int bi = -1, bdefl = 0, nsolved = 0, m_unsolved = -1;
+      for (int m = 0; m <= nJ; ++m) {
+        if (!S.solved[m]) { if (m_unsolved < 0) m_unsolved = m; continue; }
+        ++nsolved;
+        const double sbm = S.sb[m];
+        mass += sbm * sbm;
+        const double sc = a.score_norm == 0 ? fabs(sbm) / sqrt(S.theta[m]) : fabs(sbm);
+        if (sc > best || (sc == best && S.theta[m] < best_th)) { best = sc; best_th = S.theta[m]; bi = m; bdefl = 0; }
+      }
+      int t = 0;
+      for (int j = 0; j < NH; ++j) {
+        if (t < nJ && S.J[t] == j) { ++t; continue; }
+        const double cj = S.cq[j];
+        mass += cj * cj;
+        const double sc = a.score_norm == 0 ? fabs(cj) / sqrt(S.d[j]) : fabs(cj);
+        if (sc > best || (sc == best && S.d[j] < best_th)) { best = sc; best_th = S.d[j]; bi = j; bdefl = 1; }
+      }
+      int cert = 1;
+      if (m_unsolved >= 0) {
+        const double rest = fmax(zeta - mass, 0.0) * (1.0 + 1e-8) + 1e-300;
+        double bound;
+        if (a.score_norm == 0) {
+          const double th_lo = m_unsolved > 0 ? S.d[S.J[m_unsolved - 1]] : lower;
+          bound = th_lo > 0.0 ? rest / th_lo : INFINITY;
+        } else {
+          bound = rest;
+        }
+        cert = best * best > bound;
+      }
+      if (phase == 0) atomicAdd(a.diag + 0, nsolved);
+      s_cert = cert;
+      s_best = bi;
+      s_best_defl = bdefl;
+    }
+    __syncthreads();
+    if (s_cert) break;
+    if (tid == 0) atomicAdd(a.diag + 1, 1);
+  }
+
+  // winner -> alpha and coarse coefficients g (Q basis), a-normalised, sign b(u, u~) > 0
+  const int bi = s_best;
+  if (bi < 0) {  // every score NaN: freeze the pair
+    if (tid == 0) { a.upd[i] = 0; a.active[i] = 0; a.status[i] = ST_NAN; }
+    return;
+  }
+  double th, alpha;
+  if (s_best_defl) {
+    const double sgn = S.cq[bi] >= 0.0 ? 1.0 : -1.0;
+    th = S.d[bi];
+    alpha = 0.0;
+    const double inv = sgn / sqrt(th);
+    for (int j = tid; j < NH; j += kSecThreads) a.g[(size_t)j * ldk + i] = (j == bi) ? inv : 0.0;
+  } else {
+    th = S.theta[bi];
+    double ny2 = 0.0;
+    {
+      const double origin = S.orig[bi], tau = S.tau[bi];
+      double acc = 0.0;
+      for (int t = tid; t < nJ; t += kSecThreads) {
+        const int j = S.J[t];
+        const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+        acc = fma(y, y, acc);
+      }
+      ny2 = block_sum(acc, red);
+    }
+    const double sgn = S.sb[bi] >= 0.0 ? 1.0 : -1.0;
+    const double na = sqrt(th) * sqrt(ny2 + 1.0);
+    alpha = sgn / (na * sq);
+    const double origin = S.orig[bi], tau = S.tau[bi];
+    for (int j = tid; j < NH; j += kSecThreads) a.g[(size_t)j * ldk + i] = -alpha * S.cq[j];
+    __syncthreads();
+    for (int t = tid; t < nJ; t += kSecThreads) {
+      const int j = S.J[t];
+      const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+      a.g[(size_t)j * ldk + i] = fma(sgn / na, y, -alpha * S.cq[j]);
+    }
+  }
+  if (tid == 0) {
+    if (!isfinite(th) || !isfinite(alpha)) {
+      a.upd[i] = 0; a.active[i] = 0; a.status[i] = ST_NAN;
+    } else {
+      a.lam[i] = th;
+      a.alpha[i] = alpha;
+      a.upd[i] = 1;
+      const double rel = fabs(th - lam_prev) / fabs(th);
+      if (rel < a.tol) { a.active[i] = 0; a.status[i] = ST_CONVERGED; }
+      else a.status[i] = ST_ACTIVE;
+    }
+  }
+}
+
+static size_t secular_smem(int NH) {
+  return sizeof(double) * (3 * (size_t)NH + 4 * ((size_t)NH + 1)) + sizeof(int) * ((size_t)NH + (size_t)NH + 1);
+}
+
+cudaError_t secular_prepare(int NH) {
+  return cudaFuncSetAttribute(k_secular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)secular_smem(NH));
+}
+
+void secular_select(const Launch& L, const SecularArgs& a) {
+  k_secular<<<a.k, kSecThreads, secular_smem(a.NH), L.s>>>(a);
+  L.bump();
+}
+
+}  // namespace pasm
