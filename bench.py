@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the PASM hot path on GB300: eigenpairs/s to 1e-9 relative
+eigenvalue error, and the achieved bandwidth / arithmetic rate of the dominant
+kernel against the measured peak.
+
+Workload (synthetic, regenerated exactly): -Laplace u = lambda u on the unit
+square, P1 elements on the (1,1)-split right-triangle mesh, fine h = 1/1024
+(1,046,529 interior DoF), coarse H = 1/16 (225 DoF), 7 grids, k = 64 pairs,
+initial pairs = prolongated coarse eigenpairs, damped Jacobi (omega = 2/3,
+2 pre / 2 post), 2 V-cycles per correction step, pairs freeze at relative
+eigenvalue change < 1e-10.
+
+A step is one correction step (Algorithm 1) for all k pairs: one replay of
+the captured CUDA graph.  value = pairs that reach 1e-9 relative error
+against the reference eigenvalues (tests/golden, ARPACK shift-invert) divided
+by the time of the S steps the slowest of them needs (S from an untimed
+calibration run of the same iteration).  Block vectors are 536 MB each, far
+above the 129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen as mg  # noqa: E402
+
+WORK = {"dim": 2, "N": 1024, "NH": 16, "k": 64, "tol": 1e-10, "target": 1e-9,
+        "golden": "square_h1024_k72", "history": "square_h1024_H16_k64_history"}
+WORKLOAD_NAME = "unit-square P1 h=1/1024 (1046529 DoF), H=1/16 (225 DoF), 7 grids, k=64"
+METRIC = "eigenpairs/s to 1e-9 rel. eigenvalue error"
+FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (measured 1.198)
+# kernel classes whose arithmetic is float64 in mixed mode (the V-cycle classes are float32 there)
+FP64_CLASSES = ("outer_rhs", "outer_res", "border", "update", "axpy", "secular")
+
+
+def load_golden(name):
+    with open(os.path.join(ROOT, "tests", "golden", name + ".txt")) as f:
+        return np.array([float(x) for x in f if not x.startswith("#") and x.strip()])
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def hierarchy():
+    return mg.build_hierarchy(WORK["dim"], WORK["N"], WORK["NH"])
+
+
+def first_reach(hist, ref, target):
+    """per pair: first step index whose relative error is <= target (or -1)"""
+    err = np.abs(hist - ref[None, :]) / ref[None, :]
+    out = np.full(hist.shape[1], -1)
+    for i in range(hist.shape[1]):
+        ok = np.where(err[:, i] <= target)[0]
+        if ok.size:
+            out[i] = int(ok[0])
+    return out
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_mode(pg, torch, H, ref, precision, steps, warmup, rank):
+    k = WORK["k"]
+    stream = torch.cuda.current_stream()
+    A = [lv.A for lv in H.levels]
+    M = [lv.M for lv in H.levels]
+    t0 = time.perf_counter()
+    ctx = pg.pasm_setup(A, M, H.P, pg.pasm_default_opts(precision=precision), stream.cuda_stream)
+    setup_s = time.perf_counter() - t0
+    # calibration (untimed): iterate from the coarse start, record eigenvalues per step
+    pg.pasm_init(ctx, k, WORK["tol"])
+    lam = np.zeros(k)
+    hist = [None]
+    pg.pasm_get(ctx, lam)
+    hist[0] = lam.copy()
+    for _ in range(60):
+        act = pg.pasm_step(ctx)
+        pg.pasm_get(ctx, lam)
+        hist.append(lam.copy())
+        if act == 0:
+            break
+    hist = np.array(hist)
+    reach = first_reach(hist, ref, WORK["target"])
+    conv = int((reach >= 0).sum())
+    S = int(reach.max()) if conv else len(hist) - 1
+    launches = pg.pasm_last_launches(ctx)
+    # timed: W warm-up steps then exactly K steps of the captured graph
+    pg.pasm_init(ctx, k, WORK["tol"])
+    for _ in range(warmup):
+        pg.pasm_step_async(ctx)
+    torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as cs:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            pg.pasm_step_async(ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if torch.distributed.is_initialized():
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    ms_step = ms / steps
+    # per-kernel-class event timing of a few eager steps (same arithmetic)
+    trace = {}
+    for _ in range(3):
+        for name, (t_ms, by, fl, n) in pg.pasm_trace_step(ctx).items():
+            a = trace.setdefault(name, [0.0, 0.0, 0.0, 0])
+            a[0] += t_ms; a[1] += by; a[2] += fl; a[3] += n
+    pg.pasm_destroy(ctx)
+    return {"setup_s": setup_s, "S": S, "converged": conv, "reach": reach.tolist(), "ms_per_step": ms_step,
+            "launches_per_step": launches, "trace": trace, "clocks": cs.summary(), "final_lam": hist[-1].tolist()}
+
+
+def run_e2e(pg, torch, H, S, precision):
+    """End to end through pasm_solve with host buffers: the initial pairs go in
+    from pinned host memory, the eigenpairs come back to pinned host memory."""
+    k = WORK["k"]
+    A = [lv.A for lv in H.levels]
+    M = [lv.M for lv in H.levels]
+    ctx = pg.pasm_setup(A, M, H.P, pg.pasm_default_opts(precision=precision, max_steps=S),
+                        torch.cuda.current_stream().cuda_stream)
+    n = H.fine.n
+    pg.pasm_init(ctx, k, WORK["tol"])
+    lam0 = torch.zeros(k, dtype=torch.float64).pin_memory()
+    U0 = torch.zeros((n, k), dtype=torch.float64).pin_memory()
+    pg.pasm_get(ctx, lam0.numpy(), U0.numpy())
+    lam = torch.zeros(k, dtype=torch.float64).pin_memory()
+    U = torch.zeros((n, k), dtype=torch.float64).pin_memory()
+    steps = np.zeros(k, dtype=np.int32)
+    status = np.zeros(k, dtype=np.int32)
+    pg.pasm_solve(ctx, k, WORK["tol"], lam0.numpy(), U0.numpy(), lam.numpy(), U.numpy(), steps, status)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pg.pasm_solve(ctx, k, WORK["tol"], lam0.numpy(), U0.numpy(), lam.numpy(), U.numpy(), steps, status)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    pg.pasm_destroy(ctx)
+    nbytes_in = (n * k + k) * 8
+    nbytes_out = (n * k + k) * 8 + 2 * k * 4
+    return dt, nbytes_in, nbytes_out
+
+
+def oracle_sample(H, k_sample, n_steps):
+    """CPU baseline: the oracle (test infrastructure) on a bounded sample of the
+    same workload -- k_sample pairs for n_steps correction steps."""
+    import oracle
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, k_sample)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        lam, U, _ = oracle.correction(prob, lam, U)
+    return (time.perf_counter() - t0) / n_steps
+
+
+def reference_counts():
+    """steps to 1e-9 and converged pairs of the oracle's own iteration on the
+    full workload (tests/golden, written by the oracle)."""
+    p = os.path.join(ROOT, "tests", "golden", WORK["history"] + ".json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    ref = load_golden(WORK["golden"])[:WORK["k"]]
+    reach = first_reach(np.array(d["history"]), ref, WORK["target"])
+    conv = int((reach >= 0).sum())
+    return (int(reach.max()) if conv else len(d["history"]) - 1), conv
+
+
+def main_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    from paper_1908_10251_gb300 import build
+    build.build()
+    import paper_1908_10251_gb300 as pg
+    H = hierarchy()
+    ref = load_golden(WORK["golden"])[:WORK["k"]]
+    res = {}
+    for name, prec in (("mixed", 1), ("fp64", 0)):
+        res[name] = run_mode(pg, torch, H, ref, prec, args.steps, args.warmup, rank)
+    main = res["mixed"]
+    S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
+    value = world * conv / (S * ms_step / 1e3)
+    e2e_s, bin_, bout = run_e2e(pg, torch, H, S, 1)
+    e2e_value = world * conv / e2e_s
+    # dominant kernel class of the primary mode
+    tr = main["trace"]
+    dom = max(tr, key=lambda q: tr[q][0])
+    d_ms, d_bytes, d_flops, d_n = tr[dom]
+    hbm, peak_kind = load_peaks()
+    gbs = d_bytes / (d_ms * 1e-3) / 1e9
+    tfs = d_flops / (d_ms * 1e-3) / 1e12
+    fp64_heavy = dom in FP64_CLASSES and tfs / FP64_PEAK_TFLOPS > gbs / hbm
+    if fp64_heavy:
+        ach = tfs
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s (fp64)", "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "achieved_gbs": round(d_bytes / (d_ms * 1e-3) / 1e9, 1),
+                "peak_note": "fp64 FMA peak derived from 2 FMA/clk/SM x 152 SMs x 2.07 GHz"}
+    else:
+        ach = d_bytes / (d_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_note": "of %s" % peak_kind}
+    roof["launches_per_step"] = d_n / 3.0
+    roof["avg_launch_us"] = round(d_ms / d_n * 1e3, 2)
+    classes = {q: {"ms_per_step": round(v[0] / 3, 4), "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0,
+                   "GFLOPs": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0, "launches": v[3] // 3}
+               for q, v in sorted(tr.items(), key=lambda kv: -kv[1][0])}
+    # CPU baseline (oracle), bounded sample on rank 0
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ks = 2
+        t_step = oracle_sample(H, ks, 1)
+        cpu_val = conv / ((WORK["k"] / ks) * S * t_step)
+        cpu = {"value": cpu_val, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle correction step on %d of %d pairs of the same workload, 1 step (%.1f s); "
+                         "scaled by k/%d x S=%d steps" % (ks, WORK["k"], t_step, ks, S)}
+    out = {
+        "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": "mixed: f32 V-cycles under f64 residuals",
+                   "pairs_converged": conv, "pairs": WORK["k"], "steps_to_1e-9": S,
+                   "l2": "inputs larger than L2 (536 MB block vectors)", "parallelism": "replicas"},
+        "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": bin_ // max(S, 1),
+                "d2h_bytes_per_step": bout // max(S, 1), "seconds": e2e_s,
+                "note": "pasm_solve with pinned host inputs/outputs, S steps per call"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "gpu_launches": int(args.steps * main["launches_per_step"]),
+        "clocks": main["clocks"],
+        "kernels": classes,
+        "variants": {"fp64": {"value": world * res["fp64"]["converged"] / (res["fp64"]["S"] *
+                                                                           res["fp64"]["ms_per_step"] / 1e3),
+                              "ms_per_step": res["fp64"]["ms_per_step"], "steps_to_1e-9": res["fp64"]["S"],
+                              "pairs_converged": res["fp64"]["converged"], "clocks": res["fp64"]["clocks"]}},
+        "setup_s": main["setup_s"],
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    H = hierarchy()
+    counts = reference_counts()
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration history table missing"}))
+        return
+    S, conv = counts
+    ks = 2
+    times = [oracle_sample(H, ks, 1) for _ in range(max(args.steps, 1))]
+    t_step = statistics.median(times)
+    value = conv / ((WORK["k"] / ks) * S * t_step)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 * WORK["k"] / ks,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "precision": "f64 oracle", "pairs_converged": conv,
+                   "steps_to_1e-9": S},
+        "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d of %d pairs per step, %d steps; scaled by k/%d x S" % (ks, WORK["k"],
+                                                                                              len(times), ks)},
+        "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

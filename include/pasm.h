@@ -164,6 +164,38 @@ int pasm_sizes(pasm_ctx* ctx, int64_t* n_fine, int32_t* n_coarse, int32_t* n_lev
  * graph is used). */
 int pasm_last_launches(pasm_ctx* ctx, int* launches);
 
+/* Kernel classes reported by pasm_trace_step. */
+enum {
+  PASM_KC_JACOBI = 0,   /* damped Jacobi sweep (multigrid smoother)               */
+  PASM_KC_JACOBI0,      /* first sweep from a zero guess                          */
+  PASM_KC_RESID,        /* multigrid residual f - A e                             */
+  PASM_KC_SPMM,         /* restriction P^T r and float64 transfer chains          */
+  PASM_KC_PROLONG,      /* prolongate and correct e += P e_c                      */
+  PASM_KC_DENSE,        /* coarse dense products (A_H^-1, Q^T, Q)                 */
+  PASM_KC_OUTER_RHS,    /* f = lambda M u and the first float64 residual          */
+  PASM_KC_OUTER_RES,    /* later float64 residuals of the defect correction       */
+  PASM_KC_AXPY,         /* x += e                                                 */
+  PASM_KC_BORDER,       /* A u~, M u~, beta, zeta partial sums                    */
+  PASM_KC_COLSUM,       /* reduction of the partial sums                          */
+  PASM_KC_INIT,         /* coarse initial state                                   */
+  PASM_KC_SECULAR,      /* bordered eigenproblem: secular roots and selection     */
+  PASM_KC_UPDATE,       /* u = alpha u~ + P_c u_H                                 */
+  PASM_KC_COUNT,        /* active-pair count                                      */
+  PASM_KC_CAST,         /* precision conversion                                   */
+  PASM_KC_N
+};
+
+/* Run one correction step (same arithmetic as pasm_step, so the pair state
+ * advances) eagerly with a CUDA event pair around every kernel launch, and
+ * accumulate per kernel class: elapsed milliseconds, algorithmic bytes (the
+ * compulsory traffic of each launch: matrices, gathered and streamed vectors
+ * once), flops, and launch counts.  Each array has PASM_KC_N entries and may
+ * be NULL.  Synchronises the stream. */
+int pasm_trace_step(pasm_ctx* ctx, double* ms, double* bytes, double* flops, int* launches);
+
+/* A static name of kernel class cls ("jacobi", "border", ...). */
+const char* pasm_kernel_class_name(int cls);
+
 /* Release the context and all its device memory.  NULL is a no-op. */
 void pasm_destroy(pasm_ctx* ctx);
 

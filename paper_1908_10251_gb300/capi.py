@@ -77,6 +77,8 @@ def load_library():
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
+        "pasm_trace_step": (I, [P, P, P, P, P]),
+        "pasm_kernel_class_name": (ctypes.c_char_p, [I]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
     }
@@ -211,6 +213,24 @@ def pasm_last_launches(ctx: Context) -> int:
     n = ctypes.c_int(0)
     _check(load_library().pasm_last_launches(ctx.handle, ctypes.byref(n)), "pasm_last_launches")
     return n.value
+
+
+PASM_KC_N = 16
+
+
+def pasm_trace_step(ctx: Context):
+    """One traced correction step; returns {class name: (ms, bytes, flops, launches)}."""
+    lib = load_library()
+    ms = np.zeros(PASM_KC_N); by = np.zeros(PASM_KC_N); fl = np.zeros(PASM_KC_N)
+    la = np.zeros(PASM_KC_N, dtype=np.int32)
+    _check(lib.pasm_trace_step(ctx.handle, ms.ctypes.data, by.ctypes.data, fl.ctypes.data, la.ctypes.data),
+           "pasm_trace_step")
+    return {pasm_kernel_class_name(q): (float(ms[q]), float(by[q]), float(fl[q]), int(la[q]))
+            for q in range(PASM_KC_N) if la[q] > 0}
+
+
+def pasm_kernel_class_name(cls: int) -> str:
+    return load_library().pasm_kernel_class_name(cls).decode()
 
 
 def pasm_destroy(ctx: Context):

@@ -106,6 +106,16 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
   const int rpb = kBlock / g.tpr;
   const int grid = (S.n_rows + rpb - 1) / rpb;
   const T* av = vals<T>(S);
+  {
+    const double sz = sizeof(T), rows = S.n_rows, cols = S.n_cols, nnz = (double)S.nnz;
+    double bytes = nnz * (4.0 + sz) + (rows + 1) * 4.0 + cols * ldk * sz + rows * ldk * sz;
+    double flops = 2.0 * nnz * ldk;
+    int cls = KC_SPMM;
+    if (op == OP_JACOBI) { bytes += rows * ldk * sz + rows * sz; flops += 3.0 * rows * ldk; cls = KC_JACOBI; }
+    else if (op == OP_RESID) { bytes += rows * ldk * sz; flops += rows * ldk; cls = KC_RESID; }
+    else if (op == OP_SPMM_ADD) { bytes += rows * ldk * sz; flops += rows * ldk; cls = KC_PROLONG; }
+    L.begin(cls, bytes, flops);
+  }
   PASM_DISPATCH_CH(g.ch,
     switch (op) {
       case OP_JACOBI: k_rowop<T, CH, OP_JACOBI><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
@@ -144,6 +154,7 @@ void jacobi_zero(const Launch& L, int n, const T* dinv, T omega, const T* F, T* 
   const int64_t total = (int64_t)n * ldk;
   const int64_t nv = total / Vec16<T>::N;
   int grid = (int)std::min<int64_t>((nv + kBlock - 1) / kBlock, 152 * 16);
+  L.begin(KC_JACOBI0, (2.0 * total + n) * sizeof(T), 2.0 * total);
   k_jacobi_zero<T><<<grid, kBlock, 0, L.s>>>(total, ldk, dinv, omega, F, out);
   L.bump();
 }
@@ -250,6 +261,11 @@ void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const dou
   Geo g = geometry64(ldk);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.begin(KC_OUTER_RHS, nnz * 12.0 + 2 * (n + 1) * 4.0 + n * ldk * (16.0 + sizeof(TV)),
+            2.0 * nnz * ldk + 2.0 * n * ldk);
+  }
   PASM_DISPATCH_CH(g.ch, k_outer_rhs_res<TV, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, M.rp, M.ci,
                                                                             M.v64, lam, U, Fd, R, ldk, g.tpr));
   L.bump();
@@ -259,6 +275,10 @@ void outer_residual(const Launch& L, const DCsr& A, const double* Fd, const doub
   Geo g = geometry64(ldk);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double n = A.n_rows, nnz = (double)A.nnz;
+    L.begin(KC_OUTER_RES, nnz * 12.0 + (n + 1) * 4.0 + n * ldk * (16.0 + sizeof(TV)), 2.0 * nnz * ldk + n * ldk);
+  }
   PASM_DISPATCH_CH(g.ch, k_outer_res<TV, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, Fd, X, R, ldk,
                                                                         g.tpr));
   L.bump();
@@ -267,6 +287,7 @@ template <typename TV>
 void outer_axpy(const Launch& L, int n, const double* B, const TV* E, double* X, int ldk) {
   const int64_t total = (int64_t)n * ldk;
   int grid = (int)std::min<int64_t>((total / 2 + kBlock - 1) / kBlock, 152 * 16);
+  L.begin(KC_AXPY, (double)total * (16.0 + sizeof(TV)), (double)total);
   k_outer_axpy<TV><<<grid, kBlock, 0, L.s>>>(total, B, E, X);
   L.bump();
 }
@@ -336,6 +357,10 @@ int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double*
   int grid = std::min((A.n_rows + rpb - 1) / rpb, max_blocks);
   if (grid < 1) grid = 1;
   const size_t smem = (size_t)rpb * 2 * ldk * sizeof(double);
+  {
+    const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.begin(KC_BORDER, nnz * 12.0 + 2 * (n + 1) * 4.0 + 3.0 * n * ldk * 8.0, 2.0 * nnz * ldk + 4.0 * n * ldk);
+  }
   PASM_DISPATCH_CH(g.ch, k_border<CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, M.rp, M.ci, M.v64, X,
                                                                     YA, YM, partials, ldk, g.tpr));
   L.bump();
@@ -352,6 +377,7 @@ __global__ void k_colsum(const double* __restrict__ partials, int nblk, int widt
 
 void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out) {
   const int width = nq * ldk;
+  L.begin(KC_COLSUM, (double)nblk * width * 8.0 + width * 8.0, (double)nblk * width);
   k_colsum<<<(width + 127) / 128, 128, 0, L.s>>>(partials, nblk, width, out);
   L.bump();
 }
@@ -377,6 +403,7 @@ __global__ void k_dense_mm(int m, int p, const T* __restrict__ D, int ldd, int t
 template <typename T>
 void dense_mm(const Launch& L, int m, int p, const T* D, int ldd, bool trans, const T* B, T* C, int ldk) {
   dim3 grid((ldk + 63) / 64, m);
+  L.begin(KC_DENSE, ((double)m * p + (double)p * ldk + (double)m * ldk) * sizeof(T), 2.0 * m * p * ldk);
   k_dense_mm<T><<<grid, 64, 0, L.s>>>(m, p, D, ldd, trans ? 1 : 0, B, C, ldk);
   L.bump();
 }
@@ -395,6 +422,7 @@ __global__ void k_coarse_init(int NH, int k, const double* __restrict__ Q, const
 void coarse_init(const Launch& L, int NH, int k, const double* Q, const double* lamH, double* W0, double* lam,
                  int ldk) {
   dim3 grid((ldk + 63) / 64, NH);
+  L.begin(KC_INIT, (double)NH * ldk * 16.0, 0.0);
   k_coarse_init<<<grid, 64, 0, L.s>>>(NH, k, Q, lamH, W0, lam, ldk);
   L.bump();
 }
@@ -439,6 +467,11 @@ void update_pairs(const Launch& L, const DCsr& P, const double* W, const double*
   Geo g = geometry64(ldk);
   const int rpb = kBlock / g.tpr;
   const int grid = (P.n_rows + rpb - 1) / rpb;
+  {
+    const double n = P.n_rows, nnz = (double)P.nnz;
+    L.begin(KC_UPDATE, nnz * 12.0 + (n + 1) * 4.0 + (double)P.n_cols * ldk * 8.0 + 3.0 * n * ldk * 8.0,
+            2.0 * nnz * ldk + 2.0 * n * ldk);
+  }
   PASM_DISPATCH_CH(g.ch, k_update<CH><<<grid, kBlock, 0, L.s>>>(P.n_rows, P.rp, P.ci, P.v64, W, X, alpha, upd, U,
                                                                  ldk, g.tpr, 0));
   L.bump();
@@ -448,6 +481,7 @@ void update_pairs_identity(const Launch& L, int n, const double* W, const double
   Geo g = geometry64(ldk);
   const int rpb = kBlock / g.tpr;
   const int grid = (n + rpb - 1) / rpb;
+  L.begin(KC_UPDATE, 4.0 * n * ldk * 8.0, 2.0 * n * ldk);
   PASM_DISPATCH_CH(g.ch, k_update<CH><<<grid, kBlock, 0, L.s>>>(n, nullptr, nullptr, nullptr, W, X, alpha, upd, U,
                                                                  ldk, g.tpr, 1));
   L.bump();
@@ -460,6 +494,7 @@ __global__ void k_count_active(const int* __restrict__ active, int k, int* out) 
   if (threadIdx.x == 0) *out = c;
 }
 void count_active(const Launch& L, const int* active, int k, int* out) {
+  L.begin(KC_COUNT, k * 4.0, 0.0);
   k_count_active<<<1, 32, 0, L.s>>>(active, k, out);
   L.bump();
 }
@@ -471,6 +506,7 @@ __global__ void k_cast_d2f(const double* __restrict__ in, float* __restrict__ ou
 void cast_d2f(const Launch& L, const double* in, float* out, int64_t count) {
   if (count == 0) return;
   int grid = (int)std::min<int64_t>((count + kBlock - 1) / kBlock, 152 * 16);
+  L.begin(KC_CAST, count * 12.0, 0.0);
   k_cast_d2f<<<grid, kBlock, 0, L.s>>>(in, out, count);
   L.bump();
 }

@@ -19,11 +19,29 @@ template <typename T> inline const T* vals(const DCsr& m);
 template <> inline const double* vals<double>(const DCsr& m) { return m.v64; }
 template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
 
-// Launch bookkeeping shared by every launcher: the stream and a launch counter.
+// Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
+enum KernelClass {
+  KC_JACOBI = 0, KC_JACOBI0, KC_RESID, KC_SPMM, KC_PROLONG, KC_DENSE, KC_OUTER_RHS, KC_OUTER_RES, KC_AXPY,
+  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_N
+};
+
+// Host-side event recorder (defined in pasm.cu); null when not tracing.
+struct Tracer;
+void tracer_begin(Tracer* t, cudaStream_t s, int cls, double bytes, double flops);
+void tracer_end(Tracer* t, cudaStream_t s);
+
+// Launch bookkeeping shared by every launcher: the stream, a launch counter
+// and an optional tracer that brackets each launch with CUDA events and
+// records its algorithmic bytes and flops.
 struct Launch {
   cudaStream_t s = nullptr;
   int* counter = nullptr;
-  void bump() const { if (counter) ++*counter; }
+  Tracer* tr = nullptr;
+  void begin(int cls, double bytes, double flops) const { if (tr) tracer_begin(tr, s, cls, bytes, flops); }
+  void bump() const {
+    if (counter) ++*counter;
+    if (tr) tracer_end(tr, s);
+  }
 };
 
 enum RowOp { OP_JACOBI = 0, OP_RESID = 1, OP_SPMM = 2, OP_SPMM_ADD = 3 };

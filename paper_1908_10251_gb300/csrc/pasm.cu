@@ -16,7 +16,34 @@
 
 namespace pasm {
 int coarse_generalized_eig(int n, const double* A, const double* M, double* lam, double* Q);
+
+struct Tracer {
+  struct Rec { int cls; double bytes, flops; int e0, e1; };
+  std::vector<cudaEvent_t> ev;
+  std::vector<Rec> recs;
+  size_t used = 0;
+  int get() {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    return (int)used++;
+  }
+  ~Tracer() { for (auto e : ev) cudaEventDestroy(e); }
+};
+void tracer_begin(Tracer* t, cudaStream_t s, int cls, double bytes, double flops) {
+  const int e0 = t->get();
+  cudaEventRecord(t->ev[(size_t)e0], s);
+  t->recs.push_back({cls, bytes, flops, e0, -1});
 }
+void tracer_end(Tracer* t, cudaStream_t s) {
+  if (t->recs.empty() || t->recs.back().e1 >= 0) return;
+  const int e1 = t->get();
+  cudaEventRecord(t->ev[(size_t)e1], s);
+  t->recs.back().e1 = e1;
+}
+}  // namespace pasm
 using namespace pasm;
 
 namespace {
@@ -62,6 +89,7 @@ struct pasm_ctx {
   int* h_nact = nullptr;  // pinned
   int max_border_blocks = 152 * 8;
   cudaGraphExec_t graph = nullptr;
+  Tracer* tracer = nullptr;  // set only inside pasm_trace_step
   int launches = 0;
   int last_launches = 0;
   bool initialized = false;
@@ -158,6 +186,7 @@ Launch launcher(pasm_ctx* c) {
   Launch L;
   L.s = c->s;
   L.counter = &c->launches;
+  L.tr = c->tracer;
   return L;
 }
 
@@ -652,6 +681,41 @@ int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, d
   if (zeta) CK(cudaMemcpyAsync(zeta, c->bz + c->ldk, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
   CK(cudaStreamSynchronize(c->s));
   return PASM_OK;
+}
+
+int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* launches) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  Scope sc(c);
+  Tracer tr;
+  c->tracer = &tr;
+  c->launches = 0;
+  step_body(c);
+  c->tracer = nullptr;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  for (int q = 0; q < KC_N; ++q) {
+    if (ms) ms[q] = 0.0;
+    if (bytes) bytes[q] = 0.0;
+    if (flops) flops[q] = 0.0;
+    if (launches) launches[q] = 0;
+  }
+  for (const auto& r : tr.recs) {
+    if (r.e1 < 0 || r.cls < 0 || r.cls >= KC_N) continue;
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, tr.ev[(size_t)r.e0], tr.ev[(size_t)r.e1]));
+    if (ms) ms[r.cls] += t;
+    if (bytes) bytes[r.cls] += r.bytes;
+    if (flops) flops[r.cls] += r.flops;
+    if (launches) launches[r.cls] += 1;
+  }
+  return PASM_OK;
+}
+
+const char* pasm_kernel_class_name(int cls) {
+  static const char* names[KC_N] = {"jacobi", "jacobi0", "resid", "spmm", "prolong", "dense", "outer_rhs",
+                                    "outer_res", "axpy", "border", "colsum", "init", "secular", "update",
+                                    "count", "cast"};
+  return (cls >= 0 && cls < KC_N) ? names[cls] : "unknown";
 }
 
 int pasm_coarse_eigs(pasm_ctx* c, double* lambda_H, double* Q) {

@@ -381,6 +381,7 @@ cudaError_t secular_prepare(int NH) {
 }
 
 void secular_select(const Launch& L, const SecularArgs& a) {
+  L.begin(KC_SECULAR, (double)a.NH * a.ldk * 8.0 * 3.0, 0.0);
   k_secular<<<a.k, kSecThreads, secular_smem(a.NH), L.s>>>(a);
   L.bump();
 }

@@ -1,0 +1,71 @@
+"""Write the reference eigenvalue tables under tests/golden/ (calls only
+meshgen and oracle/).  Run: python tests/golden/make_golden.py [name ...]
+
+Each table holds the smallest discrete eigenvalues of one synthetic workload
+(the P1 pencil of Section 2 on the named mesh), from oracle.reference
+(ARPACK shift-invert), one value per line with %.17g."""
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+import meshgen as mg  # noqa: E402
+from oracle.reference import smallest_eigenvalues  # noqa: E402
+
+TABLES = {
+    # name: (dim, N_fine, count)
+    "square_h1024_k72": (2, 1024, 72),
+    "square_h64_k16": (2, 64, 16),
+    "cube_h128_k40": (3, 128, 40),
+}
+
+
+def write(name):
+    dim, N, count = TABLES[name]
+    t = time.time()
+    A, M = mg.assemble(dim, N)
+    vals = smallest_eigenvalues(A, M, count)
+    path = os.path.join(HERE, name + ".txt")
+    with open(path, "w") as f:
+        f.write("# smallest eigenvalues of the P1 pencil, dim=%d, h=1/%d, %d values\n" % (dim, N, count))
+        f.write("# written by tests/golden/make_golden.py via oracle.reference (ARPACK shift-invert)\n")
+        for v in vals:
+            f.write("%.17g\n" % v)
+    print(name, "%.1fs" % (time.time() - t), flush=True)
+
+
+HISTORIES = {
+    # name: (dim, N_fine, N_coarse, k, tol, max_steps)
+    "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40),
+}
+
+
+def write_history(name):
+    """Eigenvalue iterates of the oracle's PASM (float64, coarse initial pairs,
+    two V-cycles per step) on one workload: one row per step, one column per
+    pair; pairs freeze once their relative change is below tol."""
+    import json
+    import oracle
+    dim, N, Nc, k, tol, max_steps = HISTORIES[name]
+    t = time.time()
+    H = mg.build_hierarchy(dim, N, Nc)
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U, steps, hist = oracle.solve(prob, k, tol=tol, max_steps=max_steps, history=True)
+    out = {"dim": dim, "N_fine": N, "N_coarse": Nc, "k": k, "tol": tol, "max_steps": max_steps,
+           "steps": [int(s) for s in steps], "history": [[float(v) for v in row] for row in hist],
+           "seconds": time.time() - t}
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f)
+    print(name, "%.1fs" % (time.time() - t), flush=True)
+
+
+if __name__ == "__main__":
+    for n in (sys.argv[1:] or list(TABLES) + list(HISTORIES)):
+        if n in HISTORIES:
+            write_history(n)
+        else:
+            write(n)
