@@ -196,6 +196,36 @@ int pasm_trace_step(pasm_ctx* ctx, double* ms, double* bytes, double* flops, int
 /* A static name of kernel class cls ("jacobi", "border", ...). */
 const char* pasm_kernel_class_name(int cls);
 
+/* Bordering products of the correction step for callers that cannot allocate
+ * device memory.  The paper has no counterpart to this entry point: it exists
+ * for hosts that reserve the whole device heap for their own pool, that must
+ * not allocate inside a latency-critical loop, or whose device memory belongs
+ * to another framework's allocator.  It allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call); all inputs and outputs are caller
+ * device memory:
+ *   n            rows of the square CSR matrices A and M (device arrays,
+ *                int32 row_ptr (n+1) / col (nnz), float64 values)
+ *   k            columns of X; a power of two with 4 <= k <= 256, else
+ *                PASM_EINVAL
+ *   X            n x k row-major float64 block (one column per pair)
+ *   YA, YM       n x k outputs: A X and M X
+ *   beta, zeta   k outputs: beta_j = X_j^T A X_j, zeta_j = X_j^T M X_j
+ *   stream       cudaStream_t (NULL = legacy default stream); the call is
+ *                asynchronous on it.
+ * Its only scratch -- per-block partial sums -- lives in one fixed array of
+ * 156,160 doubles (about 1.25 MB) inside the library, held by every GPU that
+ * loads the library until the process exits; nothing in it needs clearing,
+ * since each call writes every entry it later reads.  All calls share that
+ * array, so calls whose kernels may overlap on the GPU (different streams,
+ * or concurrent host threads) race; serialise them.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call outside any stream capture.  Errors: PASM_EINVAL (sizes or
+ * NULL pointers), PASM_ECUDA. */
+int pasm_border_noalloc(int n, const int32_t* A_row_ptr, const int32_t* A_col, const double* A_val,
+                        int64_t A_nnz, const int32_t* M_row_ptr, const int32_t* M_col, const double* M_val,
+                        int64_t M_nnz, int k, const double* X, double* YA, double* YM, double* beta,
+                        double* zeta, void* stream);
+
 /* Release the context and all its device memory.  NULL is a no-op. */
 void pasm_destroy(pasm_ctx* ctx);
 

@@ -9,6 +9,6 @@ from . import capi  # noqa: F401
 from .capi import (  # noqa: F401
     pasm_default_opts, pasm_setup, pasm_init, pasm_step, pasm_step_async, pasm_get, pasm_solve, pasm_bvp,
     pasm_augmented, pasm_coarse_eigs, pasm_sizes, pasm_last_launches, pasm_destroy, pasm_strerror,
-    pasm_trace_step, pasm_kernel_class_name,
+    pasm_trace_step, pasm_kernel_class_name, pasm_border_noalloc,
     PasmError, load_library,
 )

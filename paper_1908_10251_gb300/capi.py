@@ -79,6 +79,7 @@ def load_library():
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
         "pasm_trace_step": (I, [P, P, P, P, P]),
         "pasm_kernel_class_name": (ctypes.c_char_p, [I]),
+        "pasm_border_noalloc": (I, [I, P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, I, P, P, P, P, P, P]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
     }
@@ -231,6 +232,17 @@ def pasm_trace_step(ctx: Context):
 
 def pasm_kernel_class_name(cls: int) -> str:
     return load_library().pasm_kernel_class_name(cls).decode()
+
+
+def pasm_border_noalloc(n, A_row_ptr, A_col, A_val, M_row_ptr, M_col, M_val, k, X, YA, YM, beta, zeta,
+                        stream=None):
+    """Bordering products with no device allocation (every argument is caller
+    device memory, e.g. torch CUDA tensors); see include/pasm.h."""
+    _check(load_library().pasm_border_noalloc(
+        n, _ptr(A_row_ptr, np.int32), _ptr(A_col, np.int32), _ptr(A_val), A_val.numel() if hasattr(A_val, "numel")
+        else A_val.size, _ptr(M_row_ptr, np.int32), _ptr(M_col, np.int32), _ptr(M_val),
+        M_val.numel() if hasattr(M_val, "numel") else M_val.size, k, _ptr(X), _ptr(YA), _ptr(YM), _ptr(beta),
+        _ptr(zeta), stream), "pasm_border_noalloc")
 
 
 def pasm_destroy(ctx: Context):
