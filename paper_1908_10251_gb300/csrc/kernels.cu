@@ -367,18 +367,24 @@ int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double*
   return grid;
 }
 
-__global__ void k_colsum(const double* __restrict__ partials, int nblk, int width, double* __restrict__ out) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= width) return;
+// One block per output: its 128 threads sum strided partials, then a fixed-order
+// tree reduction (deterministic).
+__global__ void __launch_bounds__(128) k_colsum(const double* __restrict__ partials, int nblk, int width,
+                                                double* __restrict__ out) {
+  __shared__ double red[4];
+  const int t = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * width + t];
-  out[t] = s;
+  for (int b = threadIdx.x; b < nblk; b += 128) s += partials[(size_t)b * width + t];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) out[t] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
 void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out) {
   const int width = nq * ldk;
   L.begin(KC_COLSUM, (double)nblk * width * 8.0 + width * 8.0, (double)nblk * width);
-  k_colsum<<<(width + 127) / 128, 128, 0, L.s>>>(partials, nblk, width, out);
+  k_colsum<<<width, 128, 0, L.s>>>(partials, nblk, width, out);
   L.bump();
 }
 

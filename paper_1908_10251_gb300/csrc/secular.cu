@@ -83,7 +83,79 @@ __device__ __forceinline__ void secular_sums(const SecShared& S, int nJ, int m, 
   psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
 }
 
-// Root m of the secular equation (0 <= m <= nJ), computed by one warp.
+// One step of the rational model of f around the iterate (see the file
+// comment).  da = a - theta < 0 and db = b - theta > 0 are the distances to the
+// interval's poles (absent ones ignored).  Returns false if the model has no
+// root in the interval (the caller bisects).
+template <typename T>
+__device__ __forceinline__ bool rational_step(bool has_left, bool has_right, T da, T db, T th, T rho, T psi,
+                                              T dpsi, T phi, T dphi, T& s) {
+  if (has_left && has_right) {
+    const T Q1 = dpsi * da * da, P1 = psi - Q1 / da;
+    const T ft = th - rho + phi;
+    const T Q2 = (dphi + T(1)) * db * db, P2 = ft - Q2 / db;
+    const T P = P1 + P2;
+    const T A2 = P, B2 = -(P * (da + db) + Q1 + Q2), C2 = P * da * db + Q1 * db + Q2 * da;
+    const T disc = fmax(B2 * B2 - T(4) * A2 * C2, T(0));
+    const T q = T(-0.5) * (B2 + copysign(sqrt(disc), B2));
+    bool ok = false;
+    if (A2 != T(0)) { const T s1 = q / A2; if (s1 > da && s1 < db) { s = s1; ok = true; } }
+    if (q != T(0)) { const T s2 = C2 / q; if (s2 > da && s2 < db) { s = s2; ok = true; } }
+    return ok;
+  }
+  if (has_right) {  // first interval: only poles to the right
+    const T Q2 = dphi * db * db, P2 = phi - Q2 / db;
+    const T f0 = th - rho + P2;
+    const T B2 = -(db - f0), C2 = -(f0 * db + Q2);
+    const T disc = fmax(B2 * B2 - T(4) * C2, T(0));
+    const T q = T(-0.5) * (B2 + copysign(sqrt(disc), B2));
+    const T sm = (q != T(0)) ? fmin(q, C2 / q) : q;
+    if (sm < db) { s = sm; return true; }
+    return false;
+  }
+  // last interval: only poles to the left
+  const T Q1 = dpsi * da * da, P1 = psi - Q1 / da;
+  const T f0 = th - rho + P1;
+  const T B2 = -(da - f0), C2 = -(f0 * da + Q1);
+  const T disc = fmax(B2 * B2 - T(4) * C2, T(0));
+  const T q = T(-0.5) * (B2 + copysign(sqrt(disc), B2));
+  const T sm = (q != T(0)) ? fmax(q, C2 / q) : q;
+  if (sm > da) { s = sm; return true; }
+  return false;
+}
+
+// float32 pre-solve: the pole offsets d_j - origin and the weights z_j^2 of this
+// lane's share of the poles live in registers (at most kPer per lane).
+static constexpr int kPer = 32;  // supports NH <= 1024
+
+__device__ __forceinline__ void sums32(const float (&dd)[kPer], const float (&zz)[kPer], int nJ, int m, int lane,
+                                       float tau, float& psi, float& dpsi, float& phi, float& dphi) {
+  psi = dpsi = phi = dphi = 0.f;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int t = lane + 32 * q;
+    if (t < nJ) {
+      float del = dd[q] - tau;
+      if (del == 0.f) del = 1e-30f;
+      const float r = __fdividef(1.f, del);
+      const float term = zz[q] * r;
+      const float dterm = term * r;
+      if (t < m) { psi += term; dpsi += dterm; }
+      else { phi += term; dphi += dterm; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    psi += __shfl_xor_sync(0xffffffffu, psi, o);
+    dpsi += __shfl_xor_sync(0xffffffffu, dpsi, o);
+    phi += __shfl_xor_sync(0xffffffffu, phi, o);
+    dphi += __shfl_xor_sync(0xffffffffu, dphi, o);
+  }
+}
+
+// Root m of the secular equation (0 <= m <= nJ), computed by one warp: a
+// float32 rational iteration locates it, then float64 iterations from there
+// polish it (usually one or two) inside the float64 bracket.
 __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double lower, double upper, int lane,
                            int* caps) {
   const bool has_left = m > 0, has_right = m < nJ;
@@ -95,17 +167,58 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
   const double a = has_left ? S.d[S.J[m - 1]] : lower;
   const double b = has_right ? S.d[S.J[m]] : upper;
   double origin, lo, hi;
-  if (!has_left) { origin = b; lo = lower - b; hi = 0.0; }
-  else if (!has_right) { origin = a; lo = 0.0; hi = upper - a; }
+  float dd[kPer], zz[kPer];
+  auto load_offsets = [&](double org) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int t = lane + 32 * q;
+      if (t < nJ) {
+        const int j = S.J[t];
+        dd[q] = (float)(S.d[j] - org);
+        zz[q] = (float)(S.z[j] * S.z[j]);
+      } else {
+        dd[q] = 1.f; zz[q] = 0.f;
+      }
+    }
+  };
+  if (!has_left) { origin = b; lo = lower - b; hi = 0.0; load_offsets(origin); }
+  else if (!has_right) { origin = a; lo = 0.0; hi = upper - a; load_offsets(origin); }
   else {
-    const double mid = 0.5 * (a + b);
-    double psi, dpsi, phi, dphi;
-    secular_sums(S, nJ, m, 0.0, mid, lane, psi, dpsi, phi, dphi);
-    const double fmid = mid - rho + psi + phi;
-    if (fmid >= 0.0) { origin = a; lo = 0.0; hi = mid - a; }
-    else { origin = b; lo = mid - b; hi = 0.0; }
+    load_offsets(a);
+    const float half = (float)(0.5 * (b - a));
+    float psi, dpsi, phi, dphi;
+    sums32(dd, zz, nJ, m, lane, half, psi, dpsi, phi, dphi);
+    const float fmid = (float)(0.5 * (a + b) - rho) + psi + phi;
+    if (fmid >= 0.f) { origin = a; lo = 0.0; hi = 0.5 * (b - a); }
+    else { origin = b; lo = -0.5 * (b - a); hi = 0.0; load_offsets(b); }
   }
-  double tau = 0.5 * (lo + hi);
+  // float32 phase
+  double tau;
+  {
+    float flo = (float)lo, fhi = (float)hi;
+    float t32 = 0.5f * (flo + fhi);
+    const float forg = (float)origin, frho = (float)rho;
+    const float fa = (float)(a - origin), fb = (float)(b - origin);
+    for (int it = 0; it < 40; ++it) {
+      float psi, dpsi, phi, dphi;
+      sums32(dd, zz, nJ, m, lane, t32, psi, dpsi, phi, dphi);
+      const float th = forg + t32;
+      const float f = th - frho + psi + phi;
+      if (fabsf(f) <= 8.f * FLT_EPSILON * (fabsf(th) + fabsf(frho) + fabsf(psi) + fabsf(phi))) break;
+      if (f > 0.f) fhi = t32; else flo = t32;
+      if (fhi - flo <= 4.f * FLT_EPSILON * fabsf(th)) break;
+      float st = 0.f;
+      const bool ok = rational_step<float>(has_left, has_right, fa - t32, fb - t32, th, frho, psi, dpsi, phi, dphi, st);
+      float tn = t32 + st;
+      if (!ok || !(tn > flo && tn < fhi) || !isfinite(tn)) tn = 0.5f * (flo + fhi);
+      const bool tiny = fabsf(tn - t32) <= 2.f * FLT_EPSILON * fabsf(forg + tn);
+      t32 = tn;
+      if (tiny) break;
+    }
+    tau = (double)t32;
+    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+  }
+  // float64 phase
   int it = 0;
   for (; it < kMaxIter; ++it) {
     double psi, dpsi, phi, dphi;
@@ -116,42 +229,10 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
     if (fabs(f) <= eb) break;
     if (f > 0.0) hi = tau; else lo = tau;
     if (hi - lo <= 4.0 * DBL_EPSILON * fabs(th)) break;
-    double s = 0.0;
-    bool ok = false;
-    if (has_left && has_right) {
-      const double da = (a - origin) - tau, db = (b - origin) - tau;  // a - theta < 0 < b - theta
-      const double Q1 = dpsi * da * da, P1 = psi - Q1 / da;
-      const double ft = th - rho + phi;
-      const double Q2 = (dphi + 1.0) * db * db, P2 = ft - Q2 / db;
-      const double P = P1 + P2;
-      const double A2 = P, B2 = -(P * (da + db) + Q1 + Q2), C2 = P * da * db + Q1 * db + Q2 * da;
-      const double disc = fmax(B2 * B2 - 4.0 * A2 * C2, 0.0);
-      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
-      const double s1 = (A2 != 0.0) ? q / A2 : 0.0, s2 = (q != 0.0) ? C2 / q : 0.0;
-      if (A2 != 0.0 && s1 > da && s1 < db) { s = s1; ok = true; }
-      if (q != 0.0 && s2 > da && s2 < db) { s = s2; ok = true; }
-    } else if (!has_left && has_right) {
-      const double db = (b - origin) - tau;
-      const double Q2 = dphi * db * db, P2 = phi - Q2 / db;
-      const double f0 = th - rho + P2;
-      const double B2 = -(db - f0), C2 = -(f0 * db + Q2);
-      const double disc = fmax(B2 * B2 - 4.0 * C2, 0.0);
-      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
-      const double s1 = q, s2 = (q != 0.0) ? C2 / q : 0.0;
-      const double sm = fmin(s1, s2);
-      if (sm < db) { s = sm; ok = true; }
-    } else if (has_left && !has_right) {
-      const double da = (a - origin) - tau;
-      const double Q1 = dpsi * da * da, P1 = psi - Q1 / da;
-      const double f0 = th - rho + P1;
-      const double B2 = -(da - f0), C2 = -(f0 * da + Q1);
-      const double disc = fmax(B2 * B2 - 4.0 * C2, 0.0);
-      const double q = -0.5 * (B2 + copysign(sqrt(disc), B2));
-      const double s1 = q, s2 = (q != 0.0) ? C2 / q : 0.0;
-      const double sm = fmax(s1, s2);
-      if (sm > da) { s = sm; ok = true; }
-    }
-    double tn = tau + s;
+    double st = 0.0;
+    const bool ok = rational_step<double>(has_left, has_right, (a - origin) - tau, (b - origin) - tau, th, rho, psi,
+                                          dpsi, phi, dphi, st);
+    double tn = tau + st;
     if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
     const bool tiny = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(origin + tn);
     tau = tn;
@@ -183,7 +264,7 @@ __device__ __forceinline__ void root_vector_sums(const SecShared& S, int nJ, int
 __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   extern __shared__ double smem[];
   __shared__ double red[32];
-  __shared__ int s_nJ, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
+  __shared__ int s_nJ, s_m0, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
   __shared__ double s_lower, s_upper;
   const int i = blockIdx.x;
   const int NH = a.NH, ldk = a.ldk;
@@ -242,6 +323,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     }
     const double zn = sqrt(zj2);
     s_nJ = nJ;
+    s_m0 = m0;
     s_lower = (nJ ? fmin(dmin, rho) : rho) - zn;
     s_upper = (nJ ? fmax(dmax, rho) : rho) + zn;
     // phase-1 list: root 0 and a window around the root holding lambda^(l)
@@ -258,8 +340,10 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   const int nJ = s_nJ;
   const double lower = s_lower, upper = s_upper;
 
-  for (int phase = 0; phase < 2; ++phase) {
-    // solve the listed roots (phase 0) or every remaining root (phase 1)
+  for (int phase = 0; phase < 3; ++phase) {
+    // phase 0: root 0 and the window around the root holding lambda^(l);
+    // phase 1: every root up to m0 + 8; phase 2: every root
+    const int mmax = phase == 0 ? -1 : (phase == 1 ? min(nJ, s_m0 + 8) : nJ);
     if (phase == 0) {
       for (int q = warp; q < s_nlist; q += kSecWarps) {
         const int m = s_list[q];
@@ -269,14 +353,20 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
       }
     } else {
-      for (int m = warp; m <= nJ; m += kSecWarps) {
+      // warp w takes the w-th, (w+8)-th, ... unsolved root at or below mmax
+      int cnt = 0;
+      for (int m = 0; m <= mmax; ++m) {
         if (S.solved[m]) continue;
+        if ((cnt++ % kSecWarps) != warp) continue;
         solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
         double ny2, yc;
         root_vector_sums(S, nJ, m, lane, ny2, yc);
-        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
+        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); }
       }
     }
+    __syncthreads();
+    if (phase > 0)
+      for (int m = tid; m <= mmax; m += kSecThreads) S.solved[m] = 1;
     __syncthreads();
     if (tid == 0) {
       // best candidate among solved roots and deflated poles
@@ -303,6 +393,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         const double rest = fmax(zeta - mass, 0.0) * (1.0 + 1e-8) + 1e-300;
         double bound;
         if (a.score_norm == 0) {
+          // every unsolved root lies above the pole left of the smallest unsolved index
           const double th_lo = m_unsolved > 0 ? S.d[S.J[m_unsolved - 1]] : lower;
           bound = th_lo > 0.0 ? rest / th_lo : INFINITY;
         } else {
