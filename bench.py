@@ -126,7 +126,7 @@ def first_reach(hist, ref, target):
 
 # ----------------------------------------------------------------------------- our arm
 
-def run_mode(pg, torch, H, ref, precision, steps, warmup, rank):
+def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60):
     k = WORK["k"]
     stream = torch.cuda.current_stream()
     A = [lv.A for lv in H.levels]
@@ -140,7 +140,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank):
     hist = [None]
     pg.pasm_get(ctx, lam)
     hist[0] = lam.copy()
-    for _ in range(60):
+    for _ in range(calib_steps):
         act = pg.pasm_step(ctx)
         pg.pasm_get(ctx, lam)
         hist.append(lam.copy())
@@ -254,13 +254,18 @@ def main_ours(args):
     H = hierarchy()
     ref = load_golden(WORK["golden"])[:WORK["k"]]
     res = {}
-    for name, prec in (("mixed", 1), ("fp64", 0)):
-        res[name] = run_mode(pg, torch, H, ref, prec, args.steps, args.warmup, rank)
-    main = res["mixed"]
+    modes = {"both": (("mixed", 1), ("fp64", 0)), "mixed": (("mixed", 1),), "fp64": (("fp64", 0),)}[args.mode]
+    for name, prec in modes:
+        res[name] = run_mode(pg, torch, H, ref, prec, args.steps, args.warmup, rank, args.calib_steps)
+    primary, primary_prec = modes[0]
+    main = res[primary]
     S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
     value = world * conv / (S * ms_step / 1e3)
-    e2e_s, bin_, bout = run_e2e(pg, torch, H, S, 1)
-    e2e_value = world * conv / e2e_s
+    if args.no_e2e:
+        e2e_s, bin_, bout, e2e_value = None, 0, 0, None
+    else:
+        e2e_s, bin_, bout = run_e2e(pg, torch, H, S, primary_prec)
+        e2e_value = world * conv / e2e_s
     # dominant kernel class of the primary mode
     tr = main["trace"]
     dom = max(tr, key=lambda q: tr[q][0])
@@ -296,8 +301,9 @@ def main_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "precision": "mixed: f32 V-cycles under f64 residuals",
+        "vs_baseline": None, "dtype": "f32+f64" if primary == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME,
+                   "precision": "mixed: f32 V-cycles under f64 residuals" if primary == "mixed" else "f64",
                    "pairs_converged": conv, "pairs": WORK["k"], "steps_to_1e-9": S,
                    "l2": "inputs larger than L2 (536 MB block vectors)", "parallelism": "replicas"},
         "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": bin_ // max(S, 1),
@@ -308,10 +314,10 @@ def main_ours(args):
         "gpu_launches": int(args.steps * main["launches_per_step"]),
         "clocks": main["clocks"],
         "kernels": classes,
-        "variants": {"fp64": {"value": world * res["fp64"]["converged"] / (res["fp64"]["S"] *
-                                                                           res["fp64"]["ms_per_step"] / 1e3),
-                              "ms_per_step": res["fp64"]["ms_per_step"], "steps_to_1e-9": res["fp64"]["S"],
-                              "pairs_converged": res["fp64"]["converged"], "clocks": res["fp64"]["clocks"]}},
+        "variants": {name: {"value": world * r["converged"] / (r["S"] * r["ms_per_step"] / 1e3),
+                            "ms_per_step": r["ms_per_step"], "steps_to_1e-9": r["S"],
+                            "pairs_converged": r["converged"], "clocks": r["clocks"]}
+                     for name, r in res.items() if name != primary},
         "setup_s": main["setup_s"],
     }
     if rank == 0:
@@ -354,6 +360,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--mode", default="both", choices=["both", "mixed", "fp64"],
+                    help="precision modes to run (the first one listed is the primary)")
+    ap.add_argument("--calib-steps", type=int, default=60, help="step cap of the calibration run")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

@@ -37,6 +37,53 @@ static Geo geometry(int ldk) {
     default: break;                                        \
   }
 
+// acc += a_p * X[ci_p, cols] for the N entries p .. p+N-1 (all valid): the N
+// index/value loads first, then the N row gathers, then the FMAs, so N
+// gathers are in flight at once.  With dscale, a_p is scaled by
+// omega * dscale[ci_p].
+template <typename T, int CH, int N>
+__device__ __forceinline__ void gather_group(const int* __restrict__ ci, const T* __restrict__ av,
+                                             const T* __restrict__ dscale, T omega, const T* __restrict__ X, int p,
+                                             int lane, int tpr, int ldk, T (&acc)[CH][Vec16<T>::N]) {
+  constexpr int V = Vec16<T>::N;
+  int j[N];
+  T a[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    j[u] = __ldg(ci + p + u);
+    a[u] = __ldg(av + p + u);
+  }
+  if (dscale) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) a[u] *= omega * __ldg(dscale + j[u]);
+  }
+  T x[N][CH][V];
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) ldg16<T>(X + (size_t)j[u] * ldk + (c * tpr + lane) * V, x[u][c]);
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[c][v] = fma(a[u], x[u][c][v], acc[c][v]);
+}
+
+// acc += sum_{p0 <= p < p1} a_p * X[ci_p, cols]: full groups of 4 entries, then
+// an exact group of the remaining 1-3 (no padded loads, no wasted FMAs).
+template <typename T, int CH>
+__device__ __forceinline__ void gather_rows(const int* __restrict__ ci, const T* __restrict__ av,
+                                            const T* __restrict__ dscale, T omega, const T* __restrict__ X, int p0,
+                                            int p1, int lane, int tpr, int ldk, T (&acc)[CH][Vec16<T>::N]) {
+  int p = p0;
+  for (; p + 4 <= p1; p += 4) gather_group<T, CH, 4>(ci, av, dscale, omega, X, p, lane, tpr, ldk, acc);
+  const int rem = p1 - p;
+  if (rem == 3) gather_group<T, CH, 3>(ci, av, dscale, omega, X, p, lane, tpr, ldk, acc);
+  else if (rem == 2) gather_group<T, CH, 2>(ci, av, dscale, omega, X, p, lane, tpr, ldk, acc);
+  else if (rem == 1) gather_group<T, CH, 1>(ci, av, dscale, omega, X, p, lane, tpr, ldk, acc);
+}
+
 // ----------------------------------------------------------------------------------------------
 // Generic row operation (Jacobi sweep, residual, SpMM, SpMM + add).
 template <typename T, int CH, int OP>
@@ -54,45 +101,30 @@ __global__ void __launch_bounds__(kBlock) k_rowop(int n, const int* __restrict__
   for (int c = 0; c < CH; ++c)
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[c][v] = T(0);
-  const int p0 = rp[row], p1 = rp[row + 1];
-  for (int p = p0; p < p1; ++p) {
-    const int j = __ldg(ci + p);
-    const T a = __ldg(av + p);
-    const T* xr = X + (size_t)j * ldk;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      T x[V];
-      ldg16<T>(xr + (c * tpr + lane) * V, x);
-#pragma unroll
-      for (int v = 0; v < V; ++v) acc[c][v] = fma(a, x[v], acc[c][v]);
-    }
-  }
+  // row-aligned operands first: their loads overlap the gather's round trips
   const size_t base = (size_t)row * ldk;
+  T y[CH][V], z[CH][V];
   T w = T(0);
-  if (OP == OP_JACOBI) w = omega * dinv[row];
+  if (OP != OP_SPMM) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) Vec16<T>::load(Y + base + (c * tpr + lane) * V, y[c]);
+  }
+  if (OP == OP_JACOBI) {
+    w = omega * dinv[row];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) Vec16<T>::load(Z + base + (c * tpr + lane) * V, z[c]);
+  }
+  gather_rows<T, CH>(ci, av, nullptr, T(0), X, rp[row], rp[row + 1], lane, tpr, ldk, acc);
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const size_t off = base + (c * tpr + lane) * V;
     T r[V];
-    if (OP == OP_JACOBI) {
-      T y[V], z[V];
-      Vec16<T>::load(Y + off, y);
-      Vec16<T>::load(Z + off, z);
 #pragma unroll
-      for (int v = 0; v < V; ++v) r[v] = fma(w, y[v] - acc[c][v], z[v]);
-    } else if (OP == OP_RESID) {
-      T y[V];
-      Vec16<T>::load(Y + off, y);
-#pragma unroll
-      for (int v = 0; v < V; ++v) r[v] = y[v] - acc[c][v];
-    } else if (OP == OP_SPMM) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) r[v] = acc[c][v];
-    } else {
-      T y[V];
-      Vec16<T>::load(Y + off, y);
-#pragma unroll
-      for (int v = 0; v < V; ++v) r[v] = y[v] + acc[c][v];
+    for (int v = 0; v < V; ++v) {
+      if (OP == OP_JACOBI) r[v] = fma(w, y[c][v] - acc[c][v], z[c][v]);
+      else if (OP == OP_RESID) r[v] = y[c][v] - acc[c][v];
+      else if (OP == OP_SPMM) r[v] = acc[c][v];
+      else r[v] = y[c][v] + acc[c][v];
     }
     Vec16<T>::store(out + off, r);
   }
@@ -162,6 +194,123 @@ template void jacobi_zero<double>(const Launch&, int, const double*, double, con
 template void jacobi_zero<float>(const Launch&, int, const float*, float, const float*, float*, int);
 
 // ----------------------------------------------------------------------------------------------
+// Fused multigrid kernels (used for the float32 V-cycle, where arithmetic is
+// cheap and HBM passes are the cost).
+//
+// Two Jacobi sweeps from a zero guess in one pass:
+//   e1 = w D^-1 f,  e2 = e1 + w D^-1 (f - A e1) = w D^-1 (2 f - A (w D^-1 f)).
+template <typename T, int CH>
+__global__ void __launch_bounds__(kBlock) k_jacobi2_zero(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                          const T* __restrict__ av, const T* __restrict__ dinv,
+                                                          T omega, const T* __restrict__ F, T* __restrict__ out,
+                                                          int ldk, int tpr) {
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  T acc[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[c][v] = T(0);
+  const T w = omega * dinv[row];
+  const size_t base = (size_t)row * ldk;
+  T f[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) ldg16<T>(F + base + (c * tpr + lane) * V, f[c]);
+  gather_rows<T, CH>(ci, av, dinv, omega, F, rp[row], rp[row + 1], lane, tpr, ldk, acc);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const size_t off = base + (c * tpr + lane) * V;
+    T r[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = w * (T(2) * f[c][v] - acc[c][v]);
+    Vec16<T>::store(out + off, r);
+  }
+}
+
+// Residual and restriction in one pass: fc = R (f - A e), the residual of each
+// fine row recomputed for every coarse row that restricts it.
+template <typename T, int CH>
+__global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int* __restrict__ rrp,
+                                                            const int* __restrict__ rci, const T* __restrict__ rv,
+                                                            const int* __restrict__ arp, const int* __restrict__ aci,
+                                                            const T* __restrict__ av, const T* __restrict__ E,
+                                                            const T* __restrict__ F, T* __restrict__ out, int ldk,
+                                                            int tpr) {
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= nc) return;
+  T acc[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[c][v] = T(0);
+  const int q0 = rrp[row], q1 = rrp[row + 1];
+  for (int q = q0; q < q1; ++q) {
+    const int i = __ldg(rci + q);
+    const T wq = __ldg(rv + q);
+    T r[CH][V], ae[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      ldg16<T>(F + (size_t)i * ldk + (c * tpr + lane) * V, r[c]);
+#pragma unroll
+      for (int v = 0; v < V; ++v) ae[c][v] = T(0);
+    }
+    gather_rows<T, CH>(aci, av, nullptr, T(0), E, __ldg(arp + i), __ldg(arp + i + 1), lane, tpr, ldk, ae);
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[c][v] = fma(wq, r[c][v] - ae[c][v], acc[c][v]);
+  }
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) Vec16<T>::store(out + base + (c * tpr + lane) * V, acc[c]);
+}
+
+template <typename T>
+void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const T* F, T* out, int ldk) {
+  if (A.n_rows == 0) return;
+  Geo g = geometry<T>(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double sz = sizeof(T), rows = A.n_rows, nnz = (double)A.nnz;
+    L.begin(KC_JACOBI, nnz * (4.0 + sz) + (rows + 1) * 4.0 + rows * sz + 2.0 * rows * ldk * sz,
+            3.0 * nnz * ldk + 2.0 * rows * ldk);
+  }
+  PASM_DISPATCH_CH(g.ch, k_jacobi2_zero<T, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, vals<T>(A), dinv,
+                                                                          omega, F, out, ldk, g.tpr));
+  L.bump();
+}
+
+template <typename T>
+void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, const T* F, T* out, int ldk) {
+  if (R.n_rows == 0) return;
+  Geo g = geometry<T>(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (R.n_rows + rpb - 1) / rpb;
+  {
+    const double sz = sizeof(T), nf = A.n_rows, nc = R.n_rows;
+    L.begin(KC_RESID, (double)(A.nnz + R.nnz) * (4.0 + sz) + (nf + nc + 2) * 4.0 + 2.0 * nf * ldk * sz +
+                          nc * ldk * sz,
+            2.0 * (double)(A.nnz + R.nnz) * ldk + nf * ldk);
+  }
+  PASM_DISPATCH_CH(g.ch, k_resid_restrict<T, CH><<<grid, kBlock, 0, L.s>>>(R.n_rows, R.rp, R.ci, vals<T>(R), A.rp,
+                                                                            A.ci, vals<T>(A), E, F, out, ldk, g.tpr));
+  L.bump();
+}
+
+template void jacobi2_zero<float>(const Launch&, const DCsr&, const float*, float, const float*, float*, int);
+template void jacobi2_zero<double>(const Launch&, const DCsr&, const double*, double, const double*, double*, int);
+template void resid_restrict<float>(const Launch&, const DCsr&, const DCsr&, const float*, const float*, float*, int);
+template void resid_restrict<double>(const Launch&, const DCsr&, const DCsr&, const double*, const double*, double*,
+                                     int);
+
+// ----------------------------------------------------------------------------------------------
 // Outer float64 kernels of the defect correction.
 template <typename TV> __device__ __forceinline__ void store_vec2(TV* p, double a, double b);
 template <> __device__ __forceinline__ void store_vec2<double>(double* p, double a, double b) {
@@ -185,19 +334,7 @@ __device__ __forceinline__ void gather_row64(const int* __restrict__ rp, const i
                                              int lane, int tpr, int ldk, double (&acc)[CH][2]) {
 #pragma unroll
   for (int c = 0; c < CH; ++c) acc[c][0] = acc[c][1] = 0.0;
-  const int p0 = rp[row], p1 = rp[row + 1];
-  for (int p = p0; p < p1; ++p) {
-    const int j = __ldg(ci + p);
-    const double a = __ldg(av + p);
-    const double* xr = X + (size_t)j * ldk;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      double x[2];
-      ldg16<double>(xr + (c * tpr + lane) * 2, x);
-      acc[c][0] = fma(a, x[0], acc[c][0]);
-      acc[c][1] = fma(a, x[1], acc[c][1]);
-    }
-  }
+  gather_rows<double, CH>(ci, av, nullptr, 0.0, X, rp[row], rp[row + 1], lane, tpr, ldk, acc);
 }
 
 template <typename TV, int CH>

@@ -59,6 +59,14 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
 template <typename T>
 void jacobi_zero(const Launch& L, int n, const T* dinv, T omega, const T* F, T* out, int ldk);
 
+// Fused V-cycle kernels (see kernels.cu):
+//   jacobi2_zero:   out = two Jacobi sweeps on A e = F from e = 0
+//   resid_restrict: out (coarse) = R (F - A E)
+template <typename T>
+void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const T* F, T* out, int ldk);
+template <typename T>
+void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, const T* F, T* out, int ldk);
+
 // Fd = lam .* (M U)  and  R = Fd - A U  (float64 arithmetic, R stored as TV)
 template <typename TV>
 void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,

@@ -199,6 +199,11 @@ template <typename T> const T* dinv(const LevelDev& v);
 template <> const double* dinv<double>(const LevelDev& v) { return v.dinv64; }
 template <> const float* dinv<float>(const LevelDev& v) { return v.dinv32; }
 
+// float32 cycles use the fused kernels (HBM passes dominate); float64 cycles keep
+// the plain ones (FP64 arithmetic dominates on GB300 and fusion recomputes).
+template <typename T> struct Fused { static constexpr bool on = false; };
+template <> struct Fused<float> { static constexpr bool on = true; };
+
 template <typename T>
 T* vcycle(pasm_ctx* c, int l) {
   const Launch L = launcher(c);
@@ -212,22 +217,32 @@ T* vcycle(pasm_ctx* c, int l) {
     return E;
   }
   const T om = (T)c->opts.omega;
+  const bool fuse = Fused<T>::on;
   T* cur = E;
   T* tmp = Tm;
-  if (c->opts.nu_pre >= 1) {
+  int s = 0;
+  if (fuse && c->opts.nu_pre >= 2) {
+    jacobi2_zero<T>(L, v.A, dinv<T>(v), om, F, cur, ldk);
+    s = 2;
+  } else if (c->opts.nu_pre >= 1) {
     jacobi_zero<T>(L, v.n, dinv<T>(v), om, F, cur, ldk);
+    s = 1;
   } else {
     cudaMemsetAsync(cur, 0, sizeof(T) * (size_t)v.n * ldk, c->s);
   }
-  for (int s = 1; s < c->opts.nu_pre; ++s) {
+  for (; s < c->opts.nu_pre; ++s) {
     rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
-  rowop<T>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
-  rowop<T>(L, OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om, (T*)c->lv[l - 1].vF, ldk);
+  if (fuse) {
+    resid_restrict<T>(L, v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
+  } else {
+    rowop<T>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
+    rowop<T>(L, OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om, (T*)c->lv[l - 1].vF, ldk);
+  }
   T* ec = vcycle<T>(c, l - 1);
   rowop<T>(L, OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
-  for (int s = 0; s < c->opts.nu_post; ++s) {
+  for (s = 0; s < c->opts.nu_post; ++s) {
     rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
