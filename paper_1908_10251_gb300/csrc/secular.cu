@@ -25,7 +25,12 @@
 // steps leaving the bracket fall back to bisection.  The iterate is kept as an
 // offset tau from the nearer pole so that lambda_j - theta is formed without
 // cancellation.  Indices with |z_j| below 8 eps times the problem scale are
-// deflated: theta = lambda_j with eigenvector e_j.
+// deflated: theta = lambda_j with eigenvector e_j.  Two poles that coincide to
+// rounding (an exact degeneracy of the coarse pencil, as the symmetries of the
+// 3D Kuhn mesh produce) are merged by a rotation in their plane: one pole keeps
+// the weight z_a^2 + z_b^2, the other becomes a deflated root with eigenvector
+// (z_b e_a - z_a e_b) / r; eigenvectors of the remaining roots keep the
+// formula y_j = -z_j / (lambda_j - theta) in the original coordinates.
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -43,7 +48,11 @@ struct SecShared {
   double* d;      // NH
   double* z;      // NH
   double* cq;     // NH
-  int* J;         // NH: non-deflated indices, ascending
+  double* w;      // NH: pole weight z_j^2 (merged weight for a merged pair)
+  int* J;         // NH: poles of the secular equation, ascending
+  int* K;         // NH: indices with a nonzero eigenvector component (J and merged-away ones)
+  int* pole;      // NH: pole whose lambda enters y_i = -z_i / (lambda_pole - theta)
+  int* rot;       // NH: for an index merged away into an equal pole, that pole; else -1
   double* theta;  // NH+1 roots
   double* orig;   // NH+1 origin (pole) of each root
   double* tau;    // NH+1 offset from origin
@@ -73,10 +82,9 @@ __device__ __forceinline__ void secular_sums(const SecShared& S, int nJ, int m, 
   psi = dpsi = phi = dphi = 0.0;
   for (int t = lane; t < nJ; t += 32) {
     const int j = S.J[t];
-    const double del = (S.d[j] - origin) - tau;
-    const double q = S.z[j] / del;
-    const double term = S.z[j] * q;
-    const double dterm = q * q;
+    const double r = 1.0 / ((S.d[j] - origin) - tau);
+    const double term = S.w[j] * r;
+    const double dterm = term * r;
     if (t < m) { psi += term; dpsi += dterm; }
     else { phi += term; dphi += dterm; }
   }
@@ -175,7 +183,7 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
       if (t < nJ) {
         const int j = S.J[t];
         dd[q] = (float)(S.d[j] - org);
-        zz[q] = (float)(S.z[j] * S.z[j]);
+        zz[q] = (float)S.w[j];
       } else {
         dd[q] = 1.f; zz[q] = 0.f;
       }
@@ -184,13 +192,14 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
   if (!has_left) { origin = b; lo = lower - b; hi = 0.0; load_offsets(origin); }
   else if (!has_right) { origin = a; lo = 0.0; hi = upper - a; load_offsets(origin); }
   else {
-    load_offsets(a);
-    const float half = (float)(0.5 * (b - a));
-    float psi, dpsi, phi, dphi;
-    sums32(dd, zz, nJ, m, lane, half, psi, dpsi, phi, dphi);
-    const float fmid = (float)(0.5 * (a + b) - rho) + psi + phi;
-    if (fmid >= 0.f) { origin = a; lo = 0.0; hi = 0.5 * (b - a); }
-    else { origin = b; lo = -0.5 * (b - a); hi = 0.0; load_offsets(b); }
+    // which half holds the root: the sign of f at the midpoint, in float64 (in
+    // float32 the sum cancels badly when rho and the weights are large)
+    const double mid = 0.5 * (a + b);
+    double psi, dpsi, phi, dphi;
+    secular_sums(S, nJ, m, 0.0, mid, lane, psi, dpsi, phi, dphi);
+    if (mid - rho + psi + phi >= 0.0) { origin = a; lo = 0.0; hi = mid - a; }
+    else { origin = b; lo = mid - b; hi = 0.0; }
+    load_offsets(origin);
   }
   // float32 phase
   double tau;
@@ -206,12 +215,12 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
       const float f = th - frho + psi + phi;
       if (fabsf(f) <= 8.f * FLT_EPSILON * (fabsf(th) + fabsf(frho) + fabsf(psi) + fabsf(phi))) break;
       if (f > 0.f) fhi = t32; else flo = t32;
-      if (fhi - flo <= 4.f * FLT_EPSILON * fabsf(th)) break;
+      if (fhi - flo <= 4.f * FLT_EPSILON * fmaxf(fabsf(flo), fabsf(fhi))) break;
       float st = 0.f;
       const bool ok = rational_step<float>(has_left, has_right, fa - t32, fb - t32, th, frho, psi, dpsi, phi, dphi, st);
       float tn = t32 + st;
       if (!ok || !(tn > flo && tn < fhi) || !isfinite(tn)) tn = 0.5f * (flo + fhi);
-      const bool tiny = fabsf(tn - t32) <= 2.f * FLT_EPSILON * fabsf(forg + tn);
+      const bool tiny = fabsf(tn - t32) <= 2.f * FLT_EPSILON * fabsf(tn);
       t32 = tn;
       if (tiny) break;
     }
@@ -228,13 +237,15 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
     const double eb = 16.0 * DBL_EPSILON * (fabs(th) + fabs(rho) + fabs(psi) + fabs(phi));
     if (fabs(f) <= eb) break;
     if (f > 0.0) hi = tau; else lo = tau;
-    if (hi - lo <= 4.0 * DBL_EPSILON * fabs(th)) break;
+    // accuracy is judged on the offset tau from the pole, not on theta: the
+    // eigenvector needs lambda_pole - theta = -tau to full relative accuracy
+    if (hi - lo <= 4.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi))) break;
     double st = 0.0;
     const bool ok = rational_step<double>(has_left, has_right, (a - origin) - tau, (b - origin) - tau, th, rho, psi,
                                           dpsi, phi, dphi, st);
     double tn = tau + st;
     if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
-    const bool tiny = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(origin + tn);
+    const bool tiny = fabs(tn - tau) <= 2.0 * DBL_EPSILON * fabs(tn);
     tau = tn;
     if (tiny) break;
   }
@@ -248,13 +259,13 @@ __device__ void solve_root(const SecShared& S, int nJ, int m, double rho, double
 }
 
 // Signed b-normalised score and |y|^2 of root m (warp-cooperative).
-__device__ __forceinline__ void root_vector_sums(const SecShared& S, int nJ, int m, int lane, double& ny2,
+__device__ __forceinline__ void root_vector_sums(const SecShared& S, int nK, int m, int lane, double& ny2,
                                                  double& yc) {
   const double origin = S.orig[m], tau = S.tau[m];
   ny2 = 0.0; yc = 0.0;
-  for (int t = lane; t < nJ; t += 32) {
-    const int j = S.J[t];
-    const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+  for (int t = lane; t < nK; t += 32) {
+    const int j = S.K[t];
+    const double y = -S.z[j] / ((S.d[S.pole[j]] - origin) - tau);
     ny2 = fma(y, y, ny2);
     yc = fma(y, S.cq[j], yc);
   }
@@ -264,7 +275,7 @@ __device__ __forceinline__ void root_vector_sums(const SecShared& S, int nJ, int
 __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   extern __shared__ double smem[];
   __shared__ double red[32];
-  __shared__ int s_nJ, s_m0, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
+  __shared__ int s_nJ, s_nK, s_m0, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
   __shared__ double s_lower, s_upper;
   const int i = blockIdx.x;
   const int NH = a.NH, ldk = a.ldk;
@@ -277,12 +288,16 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   S.d = smem;
   S.z = S.d + NH;
   S.cq = S.z + NH;
-  S.theta = S.cq + NH;
+  S.w = S.cq + NH;
+  S.theta = S.w + NH;
   S.orig = S.theta + NH + 1;
   S.tau = S.orig + NH + 1;
   S.sb = S.tau + NH + 1;
   S.J = reinterpret_cast<int*>(S.sb + NH + 1);
-  S.solved = S.J + NH;
+  S.K = S.J + NH;
+  S.pole = S.K + NH;
+  S.rot = S.pole + NH;
+  S.solved = S.rot + NH;
 
   double scc = 0.0, scb = 0.0, sdcc = 0.0;
   for (int j = tid; j < NH; j += kSecThreads) {
@@ -310,19 +325,43 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   const double tolz = 8.0 * DBL_EPSILON * scale;
   const double lam_prev = a.lam[i];
   if (tid == 0) {
-    int nJ = 0, m0 = 0;
+    // poles: indices with |z_j| > tolz.  Two poles closer than told (an exact
+    // coarse degeneracy) are merged by a rotation in their plane: the second
+    // carries the weight z_a^2 + z_b^2, and the first becomes a deflated root at
+    // the same lambda with eigenvector (z_b e_a - z_a e_b) / r.
+    const double told = 64.0 * DBL_EPSILON * fabs(S.d[NH - 1]);
+    int nJ = 0, nK = 0, m0 = 0;
+    bool last_merged = false;
     double zj2 = 0.0, dmin = 0.0, dmax = 0.0;
     for (int j = 0; j < NH; ++j) {
-      if (fabs(S.z[j]) > tolz) {
-        if (nJ == 0) dmin = S.d[j];
-        dmax = S.d[j];
+      S.rot[j] = -1;
+      S.pole[j] = j;
+      if (!(fabs(S.z[j]) > tolz)) continue;
+      const double wj = S.z[j] * S.z[j];
+      if (nJ > 0 && !last_merged && S.d[j] - S.d[S.J[nJ - 1]] <= told) {
+        const int pj = S.J[nJ - 1];
+        S.rot[pj] = j;
+        S.pole[pj] = j;
+        S.w[j] = S.w[pj] + wj;
+        S.J[nJ - 1] = j;
+        last_merged = true;
+      } else {
+        S.w[j] = wj;
         S.J[nJ++] = j;
-        zj2 += S.z[j] * S.z[j];
-        if (S.d[j] < lam_prev) m0 = nJ;
+        last_merged = false;
       }
+      S.K[nK++] = j;
+      zj2 += wj;
+    }
+    for (int t = 0; t < nJ; ++t) {
+      const double dj = S.d[S.J[t]];
+      if (t == 0) dmin = dj;
+      dmax = dj;
+      if (dj < lam_prev) m0 = t + 1;
     }
     const double zn = sqrt(zj2);
     s_nJ = nJ;
+    s_nK = nK;
     s_m0 = m0;
     s_lower = (nJ ? fmin(dmin, rho) : rho) - zn;
     s_upper = (nJ ? fmax(dmax, rho) : rho) + zn;
@@ -337,7 +376,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   }
   for (int m = tid; m <= NH; m += kSecThreads) S.solved[m] = 0;
   __syncthreads();
-  const int nJ = s_nJ;
+  const int nJ = s_nJ, nK = s_nK;
   const double lower = s_lower, upper = s_upper;
 
   for (int phase = 0; phase < 3; ++phase) {
@@ -349,7 +388,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         const int m = s_list[q];
         solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
         double ny2, yc;
-        root_vector_sums(S, nJ, m, lane, ny2, yc);
+        root_vector_sums(S, nK, m, lane, ny2, yc);
         if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
       }
     } else {
@@ -360,7 +399,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         if ((cnt++ % kSecWarps) != warp) continue;
         solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
         double ny2, yc;
-        root_vector_sums(S, nJ, m, lane, ny2, yc);
+        root_vector_sums(S, nK, m, lane, ny2, yc);
         if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); }
       }
     }
@@ -380,13 +419,21 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         const double sc = a.score_norm == 0 ? fabs(sbm) / sqrt(S.theta[m]) : fabs(sbm);
         if (sc > best || (sc == best && S.theta[m] < best_th)) { best = sc; best_th = S.theta[m]; bi = m; bdefl = 0; }
       }
-      int t = 0;
       for (int j = 0; j < NH; ++j) {
-        if (t < nJ && S.J[t] == j) { ++t; continue; }
-        const double cj = S.cq[j];
-        mass += cj * cj;
-        const double sc = a.score_norm == 0 ? fabs(cj) / sqrt(S.d[j]) : fabs(cj);
-        if (sc > best || (sc == best && S.d[j] < best_th)) { best = sc; best_th = S.d[j]; bi = j; bdefl = 1; }
+        double sbj, thj;
+        int kind;
+        if (!(fabs(S.z[j]) > tolz)) {            // plain deflation: eigenvector e_j
+          sbj = S.cq[j]; thj = S.d[j]; kind = 1;
+        } else if (S.rot[j] >= 0) {             // merged away: (z_b e_j - z_j e_b) / r
+          const int b = S.rot[j];
+          const double r = sqrt(S.w[b]);
+          sbj = (S.z[b] * S.cq[j] - S.z[j] * S.cq[b]) / r; thj = S.d[b]; kind = 2;
+        } else {
+          continue;
+        }
+        mass += sbj * sbj;
+        const double sc = a.score_norm == 0 ? fabs(sbj) / sqrt(thj) : fabs(sbj);
+        if (sc > best || (sc == best && thj < best_th)) { best = sc; best_th = thj; bi = j; bdefl = kind; }
       }
       int cert = 1;
       if (m_unsolved >= 0) {
@@ -418,21 +465,32 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     return;
   }
   double th, alpha;
-  if (s_best_defl) {
+  if (s_best_defl == 1) {
     const double sgn = S.cq[bi] >= 0.0 ? 1.0 : -1.0;
     th = S.d[bi];
     alpha = 0.0;
     const double inv = sgn / sqrt(th);
     for (int j = tid; j < NH; j += kSecThreads) a.g[(size_t)j * ldk + i] = (j == bi) ? inv : 0.0;
+  } else if (s_best_defl == 2) {
+    const int b = S.rot[bi];
+    const double r = sqrt(S.w[b]);
+    const double va = S.z[b] / r, vb = -S.z[bi] / r;
+    const double sbv = va * S.cq[bi] + vb * S.cq[b];
+    const double sgn = sbv >= 0.0 ? 1.0 : -1.0;
+    th = S.d[b];
+    alpha = 0.0;
+    const double inv = sgn / sqrt(th);
+    for (int j = tid; j < NH; j += kSecThreads)
+      a.g[(size_t)j * ldk + i] = (j == bi) ? inv * va : ((j == b) ? inv * vb : 0.0);
   } else {
     th = S.theta[bi];
     double ny2 = 0.0;
     {
       const double origin = S.orig[bi], tau = S.tau[bi];
       double acc = 0.0;
-      for (int t = tid; t < nJ; t += kSecThreads) {
-        const int j = S.J[t];
-        const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+      for (int t = tid; t < nK; t += kSecThreads) {
+        const int j = S.K[t];
+        const double y = -S.z[j] / ((S.d[S.pole[j]] - origin) - tau);
         acc = fma(y, y, acc);
       }
       ny2 = block_sum(acc, red);
@@ -443,9 +501,9 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     const double origin = S.orig[bi], tau = S.tau[bi];
     for (int j = tid; j < NH; j += kSecThreads) a.g[(size_t)j * ldk + i] = -alpha * S.cq[j];
     __syncthreads();
-    for (int t = tid; t < nJ; t += kSecThreads) {
-      const int j = S.J[t];
-      const double y = -S.z[j] / ((S.d[j] - origin) - tau);
+    for (int t = tid; t < nK; t += kSecThreads) {
+      const int j = S.K[t];
+      const double y = -S.z[j] / ((S.d[S.pole[j]] - origin) - tau);
       a.g[(size_t)j * ldk + i] = fma(sgn / na, y, -alpha * S.cq[j]);
     }
   }
@@ -464,7 +522,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
 }
 
 static size_t secular_smem(int NH) {
-  return sizeof(double) * (3 * (size_t)NH + 4 * ((size_t)NH + 1)) + sizeof(int) * ((size_t)NH + (size_t)NH + 1);
+  return sizeof(double) * (4 * (size_t)NH + 4 * ((size_t)NH + 1)) + sizeof(int) * (4 * (size_t)NH + (size_t)NH + 1);
 }
 
 cudaError_t secular_prepare(int NH) {
