@@ -61,6 +61,7 @@ enum {
 enum { PASM_FP64 = 0, PASM_MIXED = 1 };           /* precision of the V-cycles   */
 enum { PASM_SCORE_A = 0, PASM_SCORE_B = 1 };      /* normalisation in the score  */
 enum { PASM_INIT_COARSE = 0, PASM_INIT_NESTED = 1 };
+enum { PASM_JACOBI = 0, PASM_LEARNED = 1 };       /* post-smoother               */
 
 /* A sparse matrix in CSR form: n_rows x n_cols, nnz entries, 32-bit indices,
  * float64 values, column indices ascending within each row. */
@@ -91,6 +92,10 @@ typedef struct {
                           every intermediate level (Algorithm 2 step 2(A))
                           [PASM_INIT_COARSE]                                     */
   int use_graph;       /* capture the finest-level step in a CUDA graph [1]      */
+  int smoother;        /* PASM_JACOBI, or PASM_LEARNED: on levels given a grid by
+                          pasm_nn_setup the first post-smoothing sweep is the
+                          learned step with a per-pair Jacobi fallback (mixed
+                          precision only) [PASM_JACOBI]                        */
 } pasm_opts;
 
 typedef struct pasm_ctx pasm_ctx;
@@ -182,6 +187,7 @@ enum {
   PASM_KC_UPDATE,       /* u = alpha u~ + P_c u_H                                 */
   PASM_KC_COUNT,        /* active-pair count                                      */
   PASM_KC_CAST,         /* precision conversion                                   */
+  PASM_KC_NN,           /* learned smoother (convolutions, training, fallback)    */
   PASM_KC_N
 };
 
@@ -195,6 +201,49 @@ int pasm_trace_step(pasm_ctx* ctx, double* ms, double* bytes, double* flops, int
 
 /* A static name of kernel class cls ("jacobi", "border", ...). */
 const char* pasm_kernel_class_name(int cls);
+
+/* ---- Learned post-smoother.  Not in the paper: the workload specification
+ * asks for a small convolutional network standing in for damped Jacobi inside
+ * the V-cycles of Algorithm 1 step 1.  Network: three bias-free 3x3
+ * convolutions 1 -> 16 -> 16 -> 1, ReLU after the first two, made odd,
+ * N(r) = (Nt(r) - Nt(-r)) / 2; on a level with an nx x ny grid view of its
+ * interior nodes (x fastest, zero outside) it maps a residual r to a
+ * correction.  Weights: 2592 float32, W1[3][3][1][16] | W2[3][3][16][16] |
+ * W3[3][3][16][1], index [dy+1][dx+1][cin][cout] multiplying pixel
+ * (y+dy, x+dx).  Training minimises L = mean_pairs |r - A N(r)|^2 / |r|^2 with
+ * Adam.  All of it needs precision = PASM_MIXED (float32 cycles). */
+
+/* Install the network: nx[l] = grid width of level l (n_l = nx * ny), 0 = do
+ * not use it on that level; weights (host or device) are copied and the Adam
+ * state is reset.  Errors: PASM_EINVAL (not mixed precision, n_l not a multiple
+ * of nx[l], NULL). */
+int pasm_nn_setup(pasm_ctx* ctx, const int32_t* nx, const float* weights);
+
+/* Current weights (2592 float32, host or device). */
+int pasm_nn_get_weights(pasm_ctx* ctx, float* weights);
+
+/* D = N(R) for the k columns of R on level `level` (n_l x k float32 row-major,
+ * host or device).  Synchronises. */
+int pasm_nn_apply(pasm_ctx* ctx, int level, int k, const float* R, float* D);
+
+/* loss L and its gradient dL/dW (2592 float32, host or device) for the
+ * residual batch R (n_l x k float32) on level `level`. */
+int pasm_nn_loss_grad(pasm_ctx* ctx, int level, int k, const float* R, double* loss, float* grad);
+
+/* `iters` Adam steps (betas 0.9, 0.999, eps 1e-8, learning rate lr) on the
+ * fixed batch R; losses[it] (host, may be NULL) receives L before step it. */
+int pasm_nn_train(pasm_ctx* ctx, int level, int k, const float* R, int iters, float lr, double* losses);
+
+/* Training data from the method's own iterations: run the multigrid solve of
+ * Algorithm 1 step 1 on the current pairs (pasm_init first) and return the
+ * residual f - A e on level `level` (>= 1) of the first V-cycle just before
+ * its post-smoothing, n_l x k float32 (host or device).  The pair state is
+ * not changed. */
+int pasm_nn_capture_residuals(pasm_ctx* ctx, int level, float* R_out);
+
+/* Per pair, how many learned steps were accepted (residual did not grow)
+ * since pasm_init or pasm_nn_setup; counts has k entries (host or device). */
+int pasm_nn_accepted(pasm_ctx* ctx, int* counts);
 
 /* Bordering products of the correction step for callers that cannot allocate
  * device memory.  The paper has no counterpart to this entry point: it exists

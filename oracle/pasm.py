@@ -48,6 +48,10 @@ class Problem:
     nu_post: int = 2
     cycles: int = 2
     score: int = SCORE_A
+    # learned post-smoother (oracle.smoother): packed weights and per-level grid
+    # widths (0 / None = plain Jacobi on that level)
+    nn_weights: object = None
+    grids: object = None
 
     def __post_init__(self):
         self.L = len(self.A) - 1
@@ -114,8 +118,28 @@ def vcycle(prob: Problem, l: int, f, x):
     fc = P.T @ (f - A @ x)
     ec = vcycle(prob, l - 1, fc, np.zeros_like(fc))
     x = x + P @ ec
-    x = jacobi(A, dinv, f, x, prob.omega, prob.nu_post)
+    nu = prob.nu_post
+    if prob.nn_weights is not None and prob.grids is not None and prob.grids[l] and nu >= 1:
+        x = learned_sweep(prob, l, f, x)
+        nu -= 1
+    x = jacobi(A, dinv, f, x, prob.omega, nu)
     return x
+
+
+def learned_sweep(prob: Problem, l: int, f, x):
+    """Learned post-smoothing step with a per-pair fallback: each column takes
+    x + N(r) if that does not increase its residual norm, else one damped
+    Jacobi step (the network is oracle.smoother.apply on the level's grid)."""
+    from . import smoother as sm
+    A, dinv = prob.A[l], prob.dinv[l]
+    nx = prob.grids[l]
+    ny = A.shape[0] // nx
+    r = f - A @ x
+    d = sm.from_grid(sm.apply(prob.nn_weights, sm.to_grid(r, nx, ny)))
+    xt = x + d
+    rt = f - A @ xt
+    ok = np.einsum("ij,ij->j", rt, rt) <= np.einsum("ij,ij->j", r, r)
+    return np.where(ok[None, :], xt, x + prob.omega * dinv[:, None] * r)
 
 
 def bvp_solve(prob: Problem, lam, U):

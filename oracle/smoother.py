@@ -1,0 +1,157 @@
+"""Oracle of the learned multigrid post-smoother (test infrastructure only).
+
+Not in the paper: the workload specification asks for a small convolutional
+smoother standing in for damped Jacobi inside the V-cycles of Algorithm 1
+step 1.  Reading (listed in the design notes): three bias-free 3x3
+convolutions 1 -> 16 -> 16 -> 1 with ReLU after the first two, made odd,
+    N(r) = (Nt(r) - Nt(-r)) / 2,
+so that N(s r) = s N(r) for every real s (a bias-free ReLU net is positively
+homogeneous; the odd part extends that to negative s) -- no normalisation of r
+is needed.  It acts on the grid view of one level: the interior nodes of an
+nx x ny grid (x fastest), zero outside (Dirichlet).  Training minimises the
+residual left after the correction,
+    L = mean_pairs |r - A N(r)|^2 / |r|^2,
+over residuals r that the method's own V-cycles produce before
+post-smoothing.  Float64 numpy, written directly from these definitions;
+gradients by hand (chain rule), pinned against finite differences and
+torch autograd in the tests.
+
+Weight layout (float): W1[3][3][1][16], W2[3][3][16][16], W3[3][3][16][1],
+concatenated in that order (144 + 2304 + 144 = 2592 values); index
+[dy+1][dx+1][cin][cout] multiplies input pixel (y+dy, x+dx).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+C = 16
+SHAPES = ((3, 3, 1, C), (3, 3, C, C), (3, 3, C, 1))
+N_WEIGHTS = sum(int(np.prod(s)) for s in SHAPES)
+
+
+def unpack(w):
+    w = np.asarray(w, dtype=np.float64)
+    out, o = [], 0
+    for s in SHAPES:
+        n = int(np.prod(s))
+        out.append(w[o:o + n].reshape(s))
+        o += n
+    return out
+
+
+def pack(ws):
+    return np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in ws])
+
+
+def init_weights(seed: int = 0):
+    """He-style random start, scaled so that N is small at first."""
+    rng = np.random.default_rng(seed)
+    ws = []
+    for s in SHAPES:
+        fan_in = s[0] * s[1] * s[2]
+        ws.append(rng.standard_normal(s) * np.sqrt(2.0 / fan_in))
+    ws[-1] *= 0.1
+    return pack(ws)
+
+
+def to_grid(v, nx, ny):
+    """Block vector (n, k) with x fastest -> images (k, ny, nx)."""
+    return np.asarray(v).T.reshape(-1, ny, nx)
+
+
+def from_grid(g):
+    k = g.shape[0]
+    return g.reshape(k, -1).T
+
+
+def conv(x, W):
+    """x: (B, ny, nx, cin), W: (3, 3, cin, cout); zero padding (Dirichlet)."""
+    B, ny, nx, cin = x.shape
+    xp = np.zeros((B, ny + 2, nx + 2, cin))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.zeros((B, ny, nx, W.shape[3]))
+    for dy in range(3):
+        for dx in range(3):
+            out += xp[:, dy:dy + ny, dx:dx + nx] @ W[dy, dx]
+    return out
+
+
+def conv_input_grad(g, W):
+    """d(sum g * conv(x, W)) / dx for g: (B, ny, nx, cout)."""
+    B, ny, nx, cout = g.shape
+    gx = np.zeros((B, ny + 2, nx + 2, W.shape[2]))
+    for dy in range(3):
+        for dx in range(3):
+            gx[:, dy:dy + ny, dx:dx + nx] += g @ W[dy, dx].T
+    return gx[:, 1:-1, 1:-1]
+
+
+def conv_weight_grad(x, g):
+    """d(sum g * conv(x, W)) / dW."""
+    B, ny, nx, cin = x.shape
+    xp = np.zeros((B, ny + 2, nx + 2, cin))
+    xp[:, 1:-1, 1:-1] = x
+    gw = np.zeros((3, 3, cin, g.shape[3]))
+    for dy in range(3):
+        for dx in range(3):
+            gw[dy, dx] = np.einsum("byxi,byxo->io", xp[:, dy:dy + ny, dx:dx + nx], g)
+    return gw
+
+
+def _branch(x, W1, W2, W3):
+    z1 = conv(x, W1)
+    a1 = np.maximum(z1, 0.0)
+    z2 = conv(a1, W2)
+    a2 = np.maximum(z2, 0.0)
+    y = conv(a2, W3)
+    return y, (x, z1, a1, z2, a2)
+
+
+def _branch_back(gy, cache, W1, W2, W3):
+    x, z1, a1, z2, a2 = cache
+    gW3 = conv_weight_grad(a2, gy)
+    ga2 = conv_input_grad(gy, W3)
+    gz2 = ga2 * (z2 > 0)
+    gW2 = conv_weight_grad(a1, gz2)
+    ga1 = conv_input_grad(gz2, W2)
+    gz1 = ga1 * (z1 > 0)
+    gW1 = conv_weight_grad(x, gz1)
+    return gW1, gW2, gW3
+
+
+def apply(w, r_grid):
+    """N(r) for images r_grid: (B, ny, nx) -> (B, ny, nx)."""
+    W1, W2, W3 = unpack(w)
+    x = r_grid[..., None]
+    yp, _ = _branch(x, W1, W2, W3)
+    ym, _ = _branch(-x, W1, W2, W3)
+    return 0.5 * (yp - ym)[..., 0]
+
+
+def loss_and_grad(w, A, R, nx, ny):
+    """L = mean_j |r_j - A N(r_j)|^2 / |r_j|^2 over the columns r_j of R (n, k)
+    and its gradient with respect to the packed weights."""
+    W1, W2, W3 = unpack(w)
+    k = R.shape[1]
+    x = to_grid(R, nx, ny)[..., None]
+    yp, cp = _branch(x, W1, W2, W3)
+    ym, cm = _branch(-x, W1, W2, W3)
+    D = from_grid(0.5 * (yp - ym)[..., 0])
+    E = R - A @ D
+    nr2 = np.einsum("ij,ij->j", R, R)
+    L = float(np.mean(np.einsum("ij,ij->j", E, E) / nr2))
+    # dL/dD = -2 A^T E / (k |r|^2); A symmetric
+    gD = -2.0 * (A.T @ (E / nr2)) / k
+    gy = to_grid(gD, nx, ny)[..., None]
+    g1 = _branch_back(0.5 * gy, cp, W1, W2, W3)
+    g2 = _branch_back(-0.5 * gy, cm, W1, W2, W3)
+    return L, pack([a + b for a, b in zip(g1, g2)])
+
+
+def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015), t counted from 1.  Returns new (w, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -25,6 +25,8 @@ PASM_PAIR_ACTIVE, PASM_PAIR_CONVERGED, PASM_PAIR_DEGENERATE, PASM_PAIR_NAN = 0, 
 PASM_FP64, PASM_MIXED = 0, 1
 PASM_SCORE_A, PASM_SCORE_B = 0, 1
 PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
+PASM_JACOBI, PASM_LEARNED = 0, 1
+NN_WEIGHTS = 2592
 
 
 class pasm_csr(ctypes.Structure):
@@ -35,7 +37,8 @@ class pasm_csr(ctypes.Structure):
 class pasm_opts(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("cycles_per_step", ctypes.c_int), ("max_steps", ctypes.c_int), ("precision", ctypes.c_int),
-                ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 class PasmError(RuntimeError):
@@ -79,6 +82,13 @@ def load_library():
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
         "pasm_trace_step": (I, [P, P, P, P, P]),
         "pasm_kernel_class_name": (ctypes.c_char_p, [I]),
+        "pasm_nn_setup": (I, [P, P, P]),
+        "pasm_nn_get_weights": (I, [P, P]),
+        "pasm_nn_apply": (I, [P, I, I, P, P]),
+        "pasm_nn_loss_grad": (I, [P, I, I, P, P, P]),
+        "pasm_nn_train": (I, [P, I, I, P, I, ctypes.c_float, P]),
+        "pasm_nn_capture_residuals": (I, [P, I, P]),
+        "pasm_nn_accepted": (I, [P, P]),
         "pasm_border_noalloc": (I, [I, P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, I, P, P, P, P, P, P]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
@@ -96,7 +106,7 @@ def _ptr(a, dtype=np.float64):
     if a is None:
         return None
     if hasattr(a, "data_ptr"):                       # torch tensor
-        want = {np.float64: "torch.float64", np.int32: "torch.int32"}[dtype]
+        want = {np.float64: "torch.float64", np.int32: "torch.int32", np.float32: "torch.float32"}[dtype]
         if str(a.dtype) != want or not a.is_contiguous():
             raise TypeError("tensor must be contiguous %s" % want)
         return a.data_ptr()
@@ -216,7 +226,7 @@ def pasm_last_launches(ctx: Context) -> int:
     return n.value
 
 
-PASM_KC_N = 16
+PASM_KC_N = 17
 
 
 def pasm_trace_step(ctx: Context):
@@ -232,6 +242,49 @@ def pasm_trace_step(ctx: Context):
 
 def pasm_kernel_class_name(cls: int) -> str:
     return load_library().pasm_kernel_class_name(cls).decode()
+
+
+def pasm_nn_setup(ctx: Context, nx, weights):
+    """nx: per-level grid width (0 = level not used); weights: 2592 float32."""
+    nx = np.ascontiguousarray(nx, dtype=np.int32)
+    _check(load_library().pasm_nn_setup(ctx.handle, nx.ctypes.data, _ptr(weights, np.float32)), "pasm_nn_setup")
+
+
+def pasm_nn_get_weights(ctx: Context):
+    w = np.zeros(NN_WEIGHTS, dtype=np.float32)
+    _check(load_library().pasm_nn_get_weights(ctx.handle, w.ctypes.data), "pasm_nn_get_weights")
+    return w
+
+
+def pasm_nn_apply(ctx: Context, level: int, R, D):
+    _check(load_library().pasm_nn_apply(ctx.handle, level, R.shape[1], _ptr(R, np.float32), _ptr(D, np.float32)),
+           "pasm_nn_apply")
+
+
+def pasm_nn_loss_grad(ctx: Context, level: int, R):
+    loss = np.zeros(1)
+    grad = np.zeros(NN_WEIGHTS, dtype=np.float32)
+    _check(load_library().pasm_nn_loss_grad(ctx.handle, level, R.shape[1], _ptr(R, np.float32), loss.ctypes.data,
+                                            grad.ctypes.data), "pasm_nn_loss_grad")
+    return float(loss[0]), grad
+
+
+def pasm_nn_train(ctx: Context, level: int, R, iters: int, lr: float):
+    losses = np.zeros(max(iters, 1))
+    _check(load_library().pasm_nn_train(ctx.handle, level, R.shape[1], _ptr(R, np.float32), iters, lr,
+                                        losses.ctypes.data), "pasm_nn_train")
+    return losses[:iters]
+
+
+def pasm_nn_capture_residuals(ctx: Context, level: int, R_out):
+    _check(load_library().pasm_nn_capture_residuals(ctx.handle, level, _ptr(R_out, np.float32)),
+           "pasm_nn_capture_residuals")
+
+
+def pasm_nn_accepted(ctx: Context, k: int):
+    out = np.zeros(k, dtype=np.int32)
+    _check(load_library().pasm_nn_accepted(ctx.handle, out.ctypes.data), "pasm_nn_accepted")
+    return out
 
 
 def pasm_border_noalloc(n, A_row_ptr, A_col, A_val, M_row_ptr, M_col, M_val, k, X, YA, YM, beta, zeta,

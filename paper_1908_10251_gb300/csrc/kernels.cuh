@@ -22,7 +22,7 @@ template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
 // Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
 enum KernelClass {
   KC_JACOBI = 0, KC_JACOBI0, KC_RESID, KC_SPMM, KC_PROLONG, KC_DENSE, KC_OUTER_RHS, KC_OUTER_RES, KC_AXPY,
-  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_N
+  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_N
 };
 
 // Host-side event recorder (defined in pasm.cu); null when not tracing.

@@ -3,6 +3,7 @@
 // (Algorithm 2 on the finest level) and the split entry points.
 #include "../../include/pasm.h"
 #include "kernels.cuh"
+#include "smoother.cuh"
 
 #include <cuda_runtime.h>
 
@@ -90,10 +91,29 @@ struct pasm_ctx {
   int max_border_blocks = 152 * 8;
   cudaGraphExec_t graph = nullptr;
   Tracer* tracer = nullptr;  // set only inside pasm_trace_step
+  // learned post-smoother
+  struct {
+    bool ready = false;
+    std::vector<int> nx, ny;                 // grid view per level (0 = none)
+    float *W = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    int t = 0;
+    NNBuf buf;                               // activations, capacity buf.cap pixel-pairs
+    int64_t vcap = 0;                        // capacity of the n x ldk temporaries
+    float *R = nullptr, *D = nullptr, *X = nullptr, *Rt = nullptr, *Es = nullptr, *gD = nullptr;
+    double *partial = nullptr, *norms = nullptr, *loss = nullptr;
+    int* accepted = nullptr;
+    std::vector<void*> allocs;
+  } nn;
+  int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
+  float* capture_buf = nullptr;
   int launches = 0;
   int last_launches = 0;
   bool initialized = false;
 };
+
+extern "C" {
+static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs);
+}
 
 namespace {
 
@@ -204,6 +224,31 @@ template <> const float* dinv<float>(const LevelDev& v) { return v.dinv32; }
 template <typename T> struct Fused { static constexpr bool on = false; };
 template <> struct Fused<float> { static constexpr bool on = true; };
 
+// Hooks before float32 post-smoothing on level l (cur = iterate after the
+// coarse correction, tmp = free buffer): the residual capture for training
+// data, and the learned smoothing step with its per-pair Jacobi fallback.
+// Returns the number of post-smoothing sweeps done (0 or 1; 1 = result in tmp).
+int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
+  const Launch L = launcher(c);
+  LevelDev& v = c->lv[l];
+  const int ldk = c->ldk;
+  if (c->capture_level == l && c->capture_buf) {
+    rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, 0.f, c->capture_buf, ldk);
+    c->capture_level = -1;
+  }
+  if (c->opts.smoother != PASM_LEARNED || !c->nn.ready || c->nn.nx[l] == 0 || c->opts.nu_post < 1) return 0;
+  auto& nn = c->nn;
+  NNGrid g{nn.nx[l], nn.ny[l], ldk, c->k};
+  const float om = (float)c->opts.omega;
+  rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, nn.R, ldk);        // r = f - A e
+  nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);                                     // d = N(r)
+  nn_add(L, (int64_t)v.n * ldk, cur, nn.D, nn.X);                                 // e + d
+  rowop<float>(L, OP_RESID, v.A, nn.X, F, nullptr, nullptr, om, nn.Rt, ldk);      // f - A (e + d)
+  nn_column_norms(L, v.n, ldk, nn.R, nn.Rt, nn.partial, nn.norms);
+  nn_select(L, v.n, ldk, cur, nn.D, nn.R, v.dinv32, om, nn.norms, tmp, nn.accepted);
+  return 1;
+}
+
 template <typename T>
 T* vcycle(pasm_ctx* c, int l) {
   const Launch L = launcher(c);
@@ -242,7 +287,10 @@ T* vcycle(pasm_ctx* c, int l) {
   }
   T* ec = vcycle<T>(c, l - 1);
   rowop<T>(L, OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
-  for (s = 0; s < c->opts.nu_post; ++s) {
+  s = 0;
+  if (Fused<T>::on) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
+  if (s == 1) std::swap(cur, tmp);
+  for (; s < c->opts.nu_post; ++s) {
     rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
@@ -418,6 +466,7 @@ void pasm_default_opts(pasm_opts* o) {
   o->score_norm = PASM_SCORE_A;
   o->init = PASM_INIT_COARSE;
   o->use_graph = 1;
+  o->smoother = PASM_JACOBI;
 }
 
 const char* pasm_strerror(int st) {
@@ -440,6 +489,7 @@ void pasm_destroy(pasm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->s);
   free_k(c);
+  for (void* p : c->nn.allocs) cudaFree(p);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_nact) cudaFreeHost(c->h_nact);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
@@ -553,7 +603,9 @@ int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* 
   if (o.nu_pre < 0 || o.nu_post < 0 || o.cycles_per_step < 1 || o.max_steps < 0 || !(o.omega > 0.0) ||
       (o.precision != PASM_FP64 && o.precision != PASM_MIXED) ||
       (o.score_norm != PASM_SCORE_A && o.score_norm != PASM_SCORE_B) ||
-      (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED))
+      (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED) ||
+      (o.smoother != PASM_JACOBI && o.smoother != PASM_LEARNED) ||
+      (o.smoother == PASM_LEARNED && o.precision != PASM_MIXED))
     return PASM_EINVAL;
   int v = validate_levels(n_levels, A, M, P);
   if (v) return v;
@@ -601,6 +653,14 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
   }
   r = set_active(c, c->active, c->steps, c->status);
   if (r) return r;
+  if (c->nn.ready) {
+    int64_t maxn = 0;
+    for (int l = 0; l < c->nlev; ++l)
+      if (c->nn.nx[(size_t)l]) maxn = std::max<int64_t>(maxn, c->lv[(size_t)l].n);
+    r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk);
+    if (r) return r;
+    CK(cudaMemsetAsync(c->nn.accepted, 0, sizeof(int) * 256, c->s));
+  }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
   c->initialized = true;
@@ -726,10 +786,183 @@ int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* 
   return PASM_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Learned post-smoother
+
+static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs) {
+  auto& nn = c->nn;
+  if (pixpairs > nn.buf.cap) {
+    const size_t m = (size_t)pixpairs * 16;
+    float** bufs[] = {&nn.buf.z1, &nn.buf.z2p, &nn.buf.z2m, &nn.buf.h, &nn.buf.gh, &nn.buf.gzp,
+                      &nn.buf.gzm, &nn.buf.gap, &nn.buf.gam, &nn.buf.gz1};
+    for (float** b : bufs) AL(nn.allocs, b, m);
+    nn.buf.cap = pixpairs;
+  }
+  if (vecs > nn.vcap) {
+    AL(nn.allocs, &nn.R, (size_t)vecs); AL(nn.allocs, &nn.D, (size_t)vecs); AL(nn.allocs, &nn.X, (size_t)vecs);
+    AL(nn.allocs, &nn.Rt, (size_t)vecs); AL(nn.allocs, &nn.Es, (size_t)vecs); AL(nn.allocs, &nn.gD, (size_t)vecs);
+    AL(nn.allocs, &nn.partial, (size_t)((vecs / 4 + 64) / 64 + 1) * 2 * 256);
+    nn.vcap = vecs;
+  }
+  return PASM_OK;
+}
+
+int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
+  if (!c || !nx || !weights) return PASM_EINVAL;
+  if (c->opts.precision != PASM_MIXED) return PASM_EINVAL;
+  auto& nn = c->nn;
+  nn.nx.assign((size_t)c->nlev, 0);
+  nn.ny.assign((size_t)c->nlev, 0);
+  int64_t maxn = 0;
+  for (int l = 0; l < c->nlev; ++l) {
+    if (nx[l] <= 0) continue;
+    const int n = c->lv[(size_t)l].n;
+    if (n % nx[l]) return PASM_EINVAL;
+    nn.nx[(size_t)l] = nx[l];
+    nn.ny[(size_t)l] = n / nx[l];
+    maxn = std::max<int64_t>(maxn, n);
+  }
+  if (!nn.W) {
+    AL(nn.allocs, &nn.W, kNNWeights); AL(nn.allocs, &nn.m, kNNWeights); AL(nn.allocs, &nn.v, kNNWeights);
+    AL(nn.allocs, &nn.grad, kNNWeights);
+    AL(nn.allocs, &nn.buf.wpart, (size_t)NNBuf::kWgradBlocks * 2304);
+    AL(nn.allocs, &nn.buf.wflip2, 2304); AL(nn.allocs, &nn.buf.wflip3, 144);
+    AL(nn.allocs, &nn.norms, 2 * 256); AL(nn.allocs, &nn.loss, 1); AL(nn.allocs, &nn.accepted, 256);
+  }
+  CK(cudaMemcpy(nn.W, weights, sizeof(float) * kNNWeights, cudaMemcpyDefault));
+  CK(cudaMemset(nn.m, 0, sizeof(float) * kNNWeights));
+  CK(cudaMemset(nn.v, 0, sizeof(float) * kNNWeights));
+  CK(cudaMemset(nn.accepted, 0, sizeof(int) * 256));
+  nn.t = 0;
+  // V-cycle use needs the n x ldk temporaries and activations of the largest grid level
+  if (c->k > 0 && maxn > 0) {
+    int r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk);
+    if (r) return r;
+  }
+  nn.ready = true;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return PASM_OK;
+}
+
+int pasm_nn_get_weights(pasm_ctx* c, float* weights) {
+  if (!c || !weights || !c->nn.W) return PASM_ESTATE;
+  CK(cudaMemcpy(weights, c->nn.W, sizeof(float) * kNNWeights, cudaMemcpyDefault));
+  return PASM_OK;
+}
+
+// copy a user n x k float block into an n x ldk2 device block (zero padding)
+static int put_block_f(pasm_ctx* c, const float* src, float* dst, int n, int k, int ldk2) {
+  CK(cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)n * ldk2, c->s));
+  CK(cudaMemcpy2DAsync(dst, sizeof(float) * ldk2, src, sizeof(float) * k, sizeof(float) * k, n, cudaMemcpyDefault,
+                       c->s));
+  return PASM_OK;
+}
+
+static int nn_level_check(pasm_ctx* c, int level, int k) {
+  if (!c || !c->nn.ready || level < 0 || level >= c->nlev || c->nn.nx[(size_t)level] == 0 || k < 1 || k > 256)
+    return PASM_EINVAL;
+  return PASM_OK;
+}
+
+int pasm_nn_apply(pasm_ctx* c, int level, int k, const float* R, float* D) {
+  int r = nn_level_check(c, level, k);
+  if (r) return r;
+  if (!R || !D) return PASM_EINVAL;
+  Scope sc(c);
+  const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  if (r) return r;
+  auto& nn = c->nn;
+  r = put_block_f(c, R, nn.R, n, k, ldk2);
+  if (r) return r;
+  NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
+  nn_forward(launcher(c), g, nn.buf, nn.W, nn.R, nn.D);
+  CK(cudaMemcpy2DAsync(D, sizeof(float) * k, nn.D, sizeof(float) * ldk2, sizeof(float) * k, n, cudaMemcpyDefault,
+                       c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+// loss and gradient for the batch already in nn.R (n x ldk2); gradient in nn.grad
+static void nn_loss_grad_dev(pasm_ctx* c, int level, int k, int ldk2) {
+  auto& nn = c->nn;
+  const Launch L = launcher(c);
+  LevelDev& v = c->lv[(size_t)level];
+  NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
+  nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
+  rowop<float>(L, OP_RESID, v.A, nn.D, nn.R, nullptr, nullptr, 0.f, nn.X, ldk2);   // E = R - A D
+  nn_column_norms(L, v.n, ldk2, nn.R, nn.X, nn.partial, nn.norms);
+  nn_loss_seed(L, (int64_t)v.n * ldk2, ldk2, k, nn.X, nn.norms, nn.Es, nn.loss);
+  rowop<float>(L, OP_SPMM, v.A, nn.Es, nullptr, nullptr, nullptr, 0.f, nn.gD, ldk2);  // dL/dD = A^T Es
+  nn_backward(L, g, nn.buf, nn.W, nn.R, nn.gD, nn.grad);
+}
+
+int pasm_nn_loss_grad(pasm_ctx* c, int level, int k, const float* R, double* loss, float* grad) {
+  int r = nn_level_check(c, level, k);
+  if (r) return r;
+  if (!R) return PASM_EINVAL;
+  Scope sc(c);
+  const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  if (!r) r = put_block_f(c, R, c->nn.R, n, k, ldk2);
+  if (r) return r;
+  nn_loss_grad_dev(c, level, k, ldk2);
+  if (loss) CK(cudaMemcpyAsync(loss, c->nn.loss, sizeof(double), cudaMemcpyDefault, c->s));
+  if (grad) CK(cudaMemcpyAsync(grad, c->nn.grad, sizeof(float) * kNNWeights, cudaMemcpyDefault, c->s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_nn_train(pasm_ctx* c, int level, int k, const float* R, int iters, float lr, double* losses) {
+  int r = nn_level_check(c, level, k);
+  if (r) return r;
+  if (!R || iters < 0 || !(lr > 0.f)) return PASM_EINVAL;
+  Scope sc(c);
+  const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  if (!r) r = put_block_f(c, R, c->nn.R, n, k, ldk2);
+  if (r) return r;
+  auto& nn = c->nn;
+  for (int it = 0; it < iters; ++it) {
+    nn_loss_grad_dev(c, level, k, ldk2);
+    if (losses) CK(cudaMemcpyAsync(losses + it, nn.loss, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    nn_adam(launcher(c), kNNWeights, nn.W, nn.grad, nn.m, nn.v, lr, ++nn.t);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {
+  if (!c || !c->initialized || level < 1 || level >= c->nlev || !R_out) return PASM_EINVAL;
+  if (c->opts.precision != PASM_MIXED) return PASM_EINVAL;
+  Scope sc(c);
+  const int n = c->lv[(size_t)level].n;
+  int r = nn_ensure(c, 0, (int64_t)n * c->ldk);
+  if (r) return r;
+  c->capture_level = level;
+  c->capture_buf = c->nn.Rt;
+  bvp(c, c->nlev - 1, c->lam, c->U, c->YA);   // scratch output; the pair state is not touched
+  c->capture_level = -1;
+  c->capture_buf = nullptr;
+  CK(cudaMemcpy2DAsync(R_out, sizeof(float) * c->k, c->nn.Rt, sizeof(float) * c->ldk, sizeof(float) * c->k, n,
+                       cudaMemcpyDefault, c->s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_nn_accepted(pasm_ctx* c, int* counts) {
+  if (!c || !counts || !c->nn.accepted || c->k < 1) return PASM_ESTATE;
+  CK(cudaMemcpy(counts, c->nn.accepted, sizeof(int) * c->k, cudaMemcpyDefault));
+  return PASM_OK;
+}
+
 const char* pasm_kernel_class_name(int cls) {
   static const char* names[KC_N] = {"jacobi", "jacobi0", "resid", "spmm", "prolong", "dense", "outer_rhs",
                                     "outer_res", "axpy", "border", "colsum", "init", "secular", "update",
-                                    "count", "cast"};
+                                    "count", "cast", "nn"};
   return (cls >= 0 && cls < KC_N) ? names[cls] : "unknown";
 }
 

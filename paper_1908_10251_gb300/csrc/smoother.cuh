@@ -1,0 +1,43 @@
+// Learned post-smoother: launchers (smoother.cu) and its buffers.
+#pragma once
+#include "kernels.cuh"
+
+namespace pasm {
+
+constexpr int kNNWeights = 144 + 2304 + 144;
+
+// Grid view of one level: nx * ny interior nodes (x fastest), ldk columns of
+// which the first k are pairs.
+struct NNGrid {
+  int nx = 0, ny = 0, ldk = 0, k = 0;
+};
+
+// Device scratch for one grid size (capacity in pixel-pairs x 16 floats).
+struct NNBuf {
+  static constexpr int kWgradBlocks = 1024;
+  int64_t cap = 0;  // pixel-pairs
+  float *z1 = nullptr, *z2p = nullptr, *z2m = nullptr, *h = nullptr;   // forward activations (x16)
+  float *gh = nullptr, *gzp = nullptr, *gzm = nullptr, *gap = nullptr, *gam = nullptr, *gz1 = nullptr;  // backward
+  float* wpart = nullptr;   // kWgradBlocks x 2304
+  float* wflip2 = nullptr;  // 2304
+  float* wflip3 = nullptr;  // 144
+};
+
+// D = N(R) on grid g (R, D: n x ldk float32)
+void nn_forward(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, const float* R, float* D);
+// gW = dL/dW given gD = dL/dD, after nn_forward on the same R (activations kept in b)
+void nn_backward(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, const float* R, const float* gD,
+                 float* gW);
+// norms[c] = |a_c|^2, norms[ldk + c] = |b_c|^2 (float64 sums); partial >= ceil(n/64) x 2 x ldk doubles
+void nn_column_norms(const Launch& L, int n, int ldk, const float* a, const float* b, double* partial,
+                     double* norms);
+// Es = -2 E / (k |r_c|^2) and loss = mean_c |E_c|^2 / |r_c|^2 from norms (|r|^2, |E|^2)
+void nn_loss_seed(const Launch& L, int64_t total, int ldk, int k, const float* E, const double* norms, float* Es,
+                  double* loss);
+void nn_adam(const Launch& L, int nw, float* w, const float* g, float* m, float* v, float lr, int t);
+void nn_add(const Launch& L, int64_t total, const float* a, const float* b, float* o);
+// out = (|R_try_c| <= |R_c|) ? E + D : E + omega dinv R   (norms from nn_column_norms(R, R_try))
+void nn_select(const Launch& L, int n, int ldk, const float* E, const float* D, const float* R, const float* dinv,
+               float omega, const double* norms, float* out, int* accepted);
+
+}  // namespace pasm

@@ -1,0 +1,111 @@
+"""Pins of the learned-smoother oracle (oracle/smoother.py): gradients against
+central finite differences and against torch autograd over an independent
+forward written with torch's conv2d, the homogeneity the odd bias-free
+construction guarantees, and Adam against torch.optim.Adam."""
+import numpy as np
+import pytest
+
+import meshgen as mg
+from oracle import smoother as sm
+
+torch = pytest.importorskip("torch")
+
+
+def small_case(seed=0, N=8, k=2):
+    A, M = mg.assemble(2, N)
+    nx = ny = N - 1
+    rng = np.random.default_rng(seed)
+    R = rng.standard_normal((nx * ny, k))
+    w = sm.init_weights(seed) * 3.0
+    return A, R, w, nx, ny
+
+
+def torch_forward(w, R, nx, ny):
+    """N(r) with torch.nn.functional.conv2d (cross-correlation, NCHW)."""
+    W1, W2, W3 = sm.unpack(w)
+    def tw(W):  # [3][3][cin][cout] -> [cout][cin][3][3]
+        return torch.tensor(np.transpose(W, (3, 2, 0, 1)))
+    x = torch.tensor(np.asarray(R).T.reshape(-1, 1, ny, nx))
+    F = torch.nn.functional
+    def branch(z):
+        a = F.relu(F.conv2d(z, tw(W1), padding=1))
+        a = F.relu(F.conv2d(a, tw(W2), padding=1))
+        return F.conv2d(a, tw(W3), padding=1)
+    return 0.5 * (branch(x) - branch(-x))
+
+
+def test_forward_matches_torch_conv2d():
+    A, R, w, nx, ny = small_case()
+    ours = sm.apply(w, sm.to_grid(R, nx, ny))
+    ref = torch_forward(w, R, nx, ny).numpy()[:, 0]
+    assert np.allclose(ours, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_gradient_matches_torch_autograd():
+    A, R, w, nx, ny = small_case(1)
+    L, g = sm.loss_and_grad(w, A, R, nx, ny)
+    wt = torch.tensor(w, requires_grad=True)
+    W1 = wt[:144].reshape(3, 3, 1, 16); W2 = wt[144:2448].reshape(3, 3, 16, 16); W3 = wt[2448:].reshape(3, 3, 16, 1)
+    F = torch.nn.functional
+    x = torch.tensor(R.T.reshape(-1, 1, ny, nx))
+    def tw(W):
+        return W.permute(3, 2, 0, 1)
+    def branch(z):
+        a = F.relu(F.conv2d(z, tw(W1), padding=1))
+        a = F.relu(F.conv2d(a, tw(W2), padding=1))
+        return F.conv2d(a, tw(W3), padding=1)
+    D = (0.5 * (branch(x) - branch(-x))).reshape(R.shape[1], -1).T
+    At = torch.tensor(A.toarray())
+    Rt = torch.tensor(R)
+    E = Rt - At @ D
+    Lt = torch.mean((E * E).sum(0) / (Rt * Rt).sum(0))
+    Lt.backward()
+    assert L == pytest.approx(Lt.item(), rel=1e-12)
+    assert np.allclose(g, wt.grad.numpy(), rtol=1e-9, atol=1e-12 * np.abs(g).max())
+
+
+def test_gradient_matches_finite_differences():
+    A, R, w, nx, ny = small_case(2)
+    L, g = sm.loss_and_grad(w, A, R, nx, ny)
+    rng = np.random.default_rng(3)
+    for idx in rng.choice(len(w), 12, replace=False):
+        h = 1e-6 * max(1.0, abs(w[idx]))
+        wp, wm = w.copy(), w.copy()
+        wp[idx] += h; wm[idx] -= h
+        fd = (sm.loss_and_grad(wp, A, R, nx, ny)[0] - sm.loss_and_grad(wm, A, R, nx, ny)[0]) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=2e-5, abs=1e-9)
+
+
+def test_odd_and_homogeneous():
+    """N(s r) = s N(r) for every real s (bias-free ReLU net, odd part)."""
+    A, R, w, nx, ny = small_case(4)
+    r = sm.to_grid(R, nx, ny)
+    base = sm.apply(w, r)
+    for s in (2.5, -1.3, 1e-3):
+        assert np.allclose(sm.apply(w, s * r), s * base, rtol=1e-12, atol=1e-15)
+
+
+def test_adam_matches_torch():
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal(50)
+    m = np.zeros(50); v = np.zeros(50)
+    wt = torch.tensor(w.copy(), requires_grad=True)
+    opt = torch.optim.Adam([wt], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(1, 4):
+        g = rng.standard_normal(50)
+        w, m, v = sm.adam_step(w, g, m, v, t, lr=1e-2)
+        opt.zero_grad(); wt.grad = torch.tensor(g); opt.step()
+    assert np.allclose(w, wt.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_zero_network_learned_sweep_is_jacobi_or_identity():
+    """With all-zero weights N(r) = 0: x + N(r) = x keeps the residual, so every
+    pair is accepted and the learned sweep leaves x unchanged."""
+    import oracle
+    from oracle import pasm as op
+    H = mg.build_hierarchy(2, 16, 4)
+    prob = oracle.Problem.from_hierarchy(H, nn_weights=np.zeros(sm.N_WEIGHTS),
+                                         grids=[lv.N - 1 for lv in H.levels])
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal((H.fine.n, 2)); x = rng.standard_normal((H.fine.n, 2))
+    assert np.array_equal(op.learned_sweep(prob, prob.L, f, x), x)
