@@ -52,6 +52,16 @@ def load_golden(name):
         return np.array([float(x) for x in f if not x.startswith("#") and x.strip()])
 
 
+def load_traffic():
+    """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    profiled kernels, from the committed ncu summary (profiles/)."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        return json.load(f)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -126,13 +136,16 @@ def first_reach(hist, ref, target):
 
 # ----------------------------------------------------------------------------- our arm
 
-def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60):
+def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, nn_weights=None):
     k = WORK["k"]
     stream = torch.cuda.current_stream()
     A = [lv.A for lv in H.levels]
     M = [lv.M for lv in H.levels]
     t0 = time.perf_counter()
-    ctx = pg.pasm_setup(A, M, H.P, pg.pasm_default_opts(precision=precision), stream.cuda_stream)
+    opts = pg.pasm_default_opts(precision=precision, smoother=1 if nn_weights is not None else 0)
+    ctx = pg.pasm_setup(A, M, H.P, opts, stream.cuda_stream)
+    if nn_weights is not None:
+        pg.pasm_nn_setup(ctx, grid_widths(H), nn_weights)
     setup_s = time.perf_counter() - t0
     # calibration (untimed): iterate from the coarse start, record eigenvalues per step
     pg.pasm_init(ctx, k, WORK["tol"])
@@ -176,13 +189,60 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60):
     ms_step = ms / steps
     # per-kernel-class event timing of a few eager steps (same arithmetic)
     trace = {}
+    fine_jacobi = []
     for _ in range(3):
         for name, (t_ms, by, fl, n) in pg.pasm_trace_step(ctx).items():
             a = trace.setdefault(name, [0.0, 0.0, 0.0, 0])
             a[0] += t_ms; a[1] += by; a[2] += fl; a[3] += n
+        fine_jacobi += [(t, b) for name, rows, t, b, f in pg.pasm_trace_launches(ctx)
+                        if name == "jacobi" and rows == H.fine.n]
+    accepted = pg.pasm_nn_accepted(ctx, k).tolist() if nn_weights is not None else None
     pg.pasm_destroy(ctx)
     return {"setup_s": setup_s, "S": S, "converged": conv, "reach": reach.tolist(), "ms_per_step": ms_step,
-            "launches_per_step": launches, "trace": trace, "clocks": cs.summary(), "final_lam": hist[-1].tolist()}
+            "launches_per_step": launches, "trace": trace, "clocks": cs.summary(), "final_lam": hist[-1].tolist(),
+            "fine_jacobi": fine_jacobi, "accepted": accepted}
+
+
+def init_weights(seed):
+    """He-style random start of the 2592 smoother weights (last layer scaled by 0.1)."""
+    rng = np.random.default_rng(seed)
+    shapes = ((3, 3, 1, 16), (3, 3, 16, 16), (3, 3, 16, 1))
+    out = []
+    for i, sh in enumerate(shapes):
+        w = rng.standard_normal(sh) * np.sqrt(2.0 / (sh[0] * sh[1] * sh[2]))
+        out.append(w * (0.1 if i == 2 else 1.0))
+    return np.concatenate([x.ravel() for x in out]).astype(np.float32)
+
+
+def grid_widths(H):
+    return np.array([lv.N - 1 for lv in H.levels], dtype=np.int32)
+
+
+def train_smoother(pg, torch, H, epochs=10, iters=20, lr=3e-3):
+    """Train the learned post-smoother on residuals the method's own first
+    V-cycles produce on this workload (captured on the level with h = 4 h_fine;
+    the network is h-independent), from the coarse start and two later steps."""
+    k = WORK["k"]
+    A = [lv.A for lv in H.levels]
+    M = [lv.M for lv in H.levels]
+    ctx = pg.pasm_setup(A, M, H.P, pg.pasm_default_opts(precision=1), torch.cuda.current_stream().cuda_stream)
+    pg.pasm_nn_setup(ctx, grid_widths(H), init_weights(0))
+    lvl = len(H.levels) - 3
+    t0 = time.perf_counter()
+    pg.pasm_init(ctx, k, WORK["tol"])
+    batches = []
+    for _ in range(3):
+        R = np.zeros((H.levels[lvl].n, k), dtype=np.float32)
+        pg.pasm_nn_capture_residuals(ctx, lvl, R)
+        batches.append(R)
+        pg.pasm_step(ctx)
+    losses = []
+    for _ in range(epochs):
+        for R in batches:
+            losses.append(float(pg.pasm_nn_train(ctx, lvl, R, iters, lr)[-1]))
+    w = pg.pasm_nn_get_weights(ctx)
+    pg.pasm_destroy(ctx)
+    return w, time.perf_counter() - t0, losses
 
 
 def run_e2e(pg, torch, H, S, precision):
@@ -257,6 +317,12 @@ def main_ours(args):
     modes = {"both": (("mixed", 1), ("fp64", 0)), "mixed": (("mixed", 1),), "fp64": (("fp64", 0),)}[args.mode]
     for name, prec in modes:
         res[name] = run_mode(pg, torch, H, ref, prec, args.steps, args.warmup, rank, args.calib_steps)
+    training = None
+    if args.learned:
+        w, train_s, losses = train_smoother(pg, torch, H)
+        res["mixed_learned"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps,
+                                        nn_weights=w)
+        training = {"seconds": train_s, "loss_first": losses[0], "loss_last": losses[-1]}
     primary, primary_prec = modes[0]
     main = res[primary]
     S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
@@ -286,6 +352,22 @@ def main_ours(args):
                 "frac": round(ach / hbm, 4), "traffic": None, "peak_note": "of %s" % peak_kind}
     roof["launches_per_step"] = d_n / 3.0
     roof["avg_launch_us"] = round(d_ms / d_n * 1e3, 2)
+    prof = load_traffic()
+    if dom in prof:
+        roof["traffic"] = prof[dom]["dram_bytes_per_launch"]
+        roof["traffic_source"] = prof[dom]["source"]
+    # the V-cycle's own roofline: finest-level float32 Jacobi sweeps (the metric's "V-cycle HBM GB/s")
+    fj = main["fine_jacobi"]
+    vcyc = None
+    if fj:
+        t_avg = sum(t for t, _ in fj) / len(fj)
+        b_avg = sum(b for _, b in fj) / len(fj)
+        ach = b_avg / (t_avg * 1e-3) / 1e9
+        vcyc = {"bound": "hbm", "kernel": "k_rowop<float,JACOBI> finest level", "achieved": round(ach, 1),
+                "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4), "avg_launch_us": round(t_avg * 1e3, 1),
+                "algorithmic_bytes_per_launch": b_avg,
+                "traffic": prof.get("jacobi_fine", {}).get("dram_bytes_per_launch"),
+                "launches_timed": len(fj), "peak_note": "of %s" % peak_kind}
     classes = {q: {"ms_per_step": round(v[0] / 3, 4), "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0,
                    "GFLOPs": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0, "launches": v[3] // 3}
                for q, v in sorted(tr.items(), key=lambda kv: -kv[1][0])}
@@ -310,13 +392,16 @@ def main_ours(args):
                 "d2h_bytes_per_step": bout // max(S, 1), "seconds": e2e_s,
                 "note": "pasm_solve with pinned host inputs/outputs, S steps per call"},
         "roofline": roof,
+        "roofline_vcycle": vcyc,
+        "smoother_training": training,
         "cpu_baseline": cpu,
         "gpu_launches": int(args.steps * main["launches_per_step"]),
         "clocks": main["clocks"],
         "kernels": classes,
         "variants": {name: {"value": world * r["converged"] / (r["S"] * r["ms_per_step"] / 1e3),
                             "ms_per_step": r["ms_per_step"], "steps_to_1e-9": r["S"],
-                            "pairs_converged": r["converged"], "clocks": r["clocks"]}
+                            "pairs_converged": r["converged"], "clocks": r["clocks"],
+                            "learned_steps_accepted": r["accepted"]}
                      for name, r in res.items() if name != primary},
         "setup_s": main["setup_s"],
     }
@@ -364,6 +449,9 @@ def main():
     ap.add_argument("--mode", default="both", choices=["both", "mixed", "fp64"],
                     help="precision modes to run (the first one listed is the primary)")
     ap.add_argument("--calib-steps", type=int, default=60, help="step cap of the calibration run")
+    ap.add_argument("--learned", dest="learned", action="store_true", default=True,
+                    help="also train the learned post-smoother and run the mixed mode with it (default)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

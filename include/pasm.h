@@ -199,6 +199,13 @@ enum {
  * be NULL.  Synchronises the stream. */
 int pasm_trace_step(pasm_ctx* ctx, double* ms, double* bytes, double* flops, int* launches);
 
+/* The launch list of the last pasm_trace_step: *count launches; for the first
+ * `max` of them the class, rows of the matrix the launch runs on (0 when not
+ * a row kernel), event-timed milliseconds, algorithmic bytes and flops.  Any
+ * array may be NULL. */
+int pasm_trace_launches(pasm_ctx* ctx, int max, int* cls, int* rows, float* ms, double* bytes, double* flops,
+                        int* count);
+
 /* A static name of kernel class cls ("jacobi", "border", ...). */
 const char* pasm_kernel_class_name(int cls);
 

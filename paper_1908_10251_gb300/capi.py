@@ -82,6 +82,7 @@ def load_library():
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
         "pasm_trace_step": (I, [P, P, P, P, P]),
         "pasm_kernel_class_name": (ctypes.c_char_p, [I]),
+        "pasm_trace_launches": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I)]),
         "pasm_nn_setup": (I, [P, P, P]),
         "pasm_nn_get_weights": (I, [P, P]),
         "pasm_nn_apply": (I, [P, I, I, P, P]),
@@ -238,6 +239,19 @@ def pasm_trace_step(ctx: Context):
            "pasm_trace_step")
     return {pasm_kernel_class_name(q): (float(ms[q]), float(by[q]), float(fl[q]), int(la[q]))
             for q in range(PASM_KC_N) if la[q] > 0}
+
+
+def pasm_trace_launches(ctx: Context):
+    """Launch list of the last pasm_trace_step: list of (class, rows, ms, bytes, flops)."""
+    lib = load_library()
+    n = ctypes.c_int(0)
+    _check(lib.pasm_trace_launches(ctx.handle, 0, None, None, None, None, None, ctypes.byref(n)), "pasm_trace_launches")
+    cls = np.zeros(n.value, dtype=np.int32); rows = np.zeros(n.value, dtype=np.int32)
+    ms = np.zeros(n.value, dtype=np.float32); by = np.zeros(n.value); fl = np.zeros(n.value)
+    _check(lib.pasm_trace_launches(ctx.handle, n.value, cls.ctypes.data, rows.ctypes.data, ms.ctypes.data,
+                                   by.ctypes.data, fl.ctypes.data, ctypes.byref(n)), "pasm_trace_launches")
+    return [(pasm_kernel_class_name(int(c)), int(r), float(t), float(b), float(f))
+            for c, r, t, b, f in zip(cls, rows, ms, by, fl)]
 
 
 def pasm_kernel_class_name(cls: int) -> str:

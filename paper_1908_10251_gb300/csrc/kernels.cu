@@ -146,6 +146,7 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
     if (op == OP_JACOBI) { bytes += rows * ldk * sz + rows * sz; flops += 3.0 * rows * ldk; cls = KC_JACOBI; }
     else if (op == OP_RESID) { bytes += rows * ldk * sz; flops += rows * ldk; cls = KC_RESID; }
     else if (op == OP_SPMM_ADD) { bytes += rows * ldk * sz; flops += rows * ldk; cls = KC_PROLONG; }
+    L.rows(S.n_rows);
     L.begin(cls, bytes, flops);
   }
   PASM_DISPATCH_CH(g.ch,
@@ -279,6 +280,7 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
     const double sz = sizeof(T), rows = A.n_rows, nnz = (double)A.nnz;
+    L.rows(A.n_rows);
     L.begin(KC_JACOBI, nnz * (4.0 + sz) + (rows + 1) * 4.0 + rows * sz + 2.0 * rows * ldk * sz,
             3.0 * nnz * ldk + 2.0 * rows * ldk);
   }
@@ -295,6 +297,7 @@ void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, c
   const int grid = (R.n_rows + rpb - 1) / rpb;
   {
     const double sz = sizeof(T), nf = A.n_rows, nc = R.n_rows;
+    L.rows(A.n_rows);
     L.begin(KC_RESID, (double)(A.nnz + R.nnz) * (4.0 + sz) + (nf + nc + 2) * 4.0 + 2.0 * nf * ldk * sz +
                           nc * ldk * sz,
             2.0 * (double)(A.nnz + R.nnz) * ldk + nf * ldk);
@@ -400,6 +403,7 @@ void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const dou
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
     const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.rows(A.n_rows);
     L.begin(KC_OUTER_RHS, nnz * 12.0 + 2 * (n + 1) * 4.0 + n * ldk * (16.0 + sizeof(TV)),
             2.0 * nnz * ldk + 2.0 * n * ldk);
   }
@@ -414,6 +418,7 @@ void outer_residual(const Launch& L, const DCsr& A, const double* Fd, const doub
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
     const double n = A.n_rows, nnz = (double)A.nnz;
+    L.rows(A.n_rows);
     L.begin(KC_OUTER_RES, nnz * 12.0 + (n + 1) * 4.0 + n * ldk * (16.0 + sizeof(TV)), 2.0 * nnz * ldk + n * ldk);
   }
   PASM_DISPATCH_CH(g.ch, k_outer_res<TV, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, Fd, X, R, ldk,
@@ -496,6 +501,7 @@ int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double*
   const size_t smem = (size_t)rpb * 2 * ldk * sizeof(double);
   {
     const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.rows(A.n_rows);
     L.begin(KC_BORDER, nnz * 12.0 + 2 * (n + 1) * 4.0 + 3.0 * n * ldk * 8.0, 2.0 * nnz * ldk + 4.0 * n * ldk);
   }
   PASM_DISPATCH_CH(g.ch, k_border<CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, A.v64, M.rp, M.ci, M.v64, X,

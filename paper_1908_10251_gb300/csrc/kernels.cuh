@@ -28,6 +28,7 @@ enum KernelClass {
 // Host-side event recorder (defined in pasm.cu); null when not tracing.
 struct Tracer;
 void tracer_begin(Tracer* t, cudaStream_t s, int cls, double bytes, double flops);
+void tracer_rows(Tracer* t, int rows);
 void tracer_end(Tracer* t, cudaStream_t s);
 
 // Launch bookkeeping shared by every launcher: the stream, a launch counter
@@ -38,6 +39,7 @@ struct Launch {
   int* counter = nullptr;
   Tracer* tr = nullptr;
   void begin(int cls, double bytes, double flops) const { if (tr) tracer_begin(tr, s, cls, bytes, flops); }
+  void rows(int n) const { if (tr) tracer_rows(tr, n); }
   void bump() const {
     if (counter) ++*counter;
     if (tr) tracer_end(tr, s);

@@ -19,10 +19,11 @@ namespace pasm {
 int coarse_generalized_eig(int n, const double* A, const double* M, double* lam, double* Q);
 
 struct Tracer {
-  struct Rec { int cls; double bytes, flops; int e0, e1; };
+  struct Rec { int cls; double bytes, flops; int e0, e1; int rows; };
   std::vector<cudaEvent_t> ev;
   std::vector<Rec> recs;
   size_t used = 0;
+  int next_rows = 0;  // rows of the next launch (set by the launcher via tracer_rows)
   int get() {
     if (used == ev.size()) {
       cudaEvent_t e;
@@ -36,8 +37,10 @@ struct Tracer {
 void tracer_begin(Tracer* t, cudaStream_t s, int cls, double bytes, double flops) {
   const int e0 = t->get();
   cudaEventRecord(t->ev[(size_t)e0], s);
-  t->recs.push_back({cls, bytes, flops, e0, -1});
+  t->recs.push_back({cls, bytes, flops, e0, -1, t->next_rows});
+  t->next_rows = 0;
 }
+void tracer_rows(Tracer* t, int rows) { t->next_rows = rows; }
 void tracer_end(Tracer* t, cudaStream_t s) {
   if (t->recs.empty() || t->recs.back().e1 >= 0) return;
   const int e1 = t->get();
@@ -99,6 +102,7 @@ struct pasm_ctx {
     int t = 0;
     NNBuf buf;                               // activations, capacity buf.cap pixel-pairs
     int64_t vcap = 0;                        // capacity of the n x ldk temporaries
+    int64_t bcap = 0;                        // capacity of the backward activations
     float *R = nullptr, *D = nullptr, *X = nullptr, *Rt = nullptr, *Es = nullptr, *gD = nullptr;
     double *partial = nullptr, *norms = nullptr, *loss = nullptr;
     int* accepted = nullptr;
@@ -112,7 +116,7 @@ struct pasm_ctx {
 };
 
 extern "C" {
-static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs);
+static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs, bool backward);
 }
 
 namespace {
@@ -657,7 +661,7 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
     int64_t maxn = 0;
     for (int l = 0; l < c->nlev; ++l)
       if (c->nn.nx[(size_t)l]) maxn = std::max<int64_t>(maxn, c->lv[(size_t)l].n);
-    r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk);
+    r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk, false);
     if (r) return r;
     CK(cudaMemsetAsync(c->nn.accepted, 0, sizeof(int) * 256, c->s));
   }
@@ -758,6 +762,9 @@ int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, d
   return PASM_OK;
 }
 
+static std::vector<Tracer::Rec> g_last_trace;  // launch list of the last traced step
+static std::vector<float> g_last_trace_ms;
+
 int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* launches) {
   if (!c || !c->initialized) return PASM_ESTATE;
   Scope sc(c);
@@ -774,10 +781,14 @@ int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* 
     if (flops) flops[q] = 0.0;
     if (launches) launches[q] = 0;
   }
+  g_last_trace.clear();
+  g_last_trace_ms.clear();
   for (const auto& r : tr.recs) {
     if (r.e1 < 0 || r.cls < 0 || r.cls >= KC_N) continue;
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, tr.ev[(size_t)r.e0], tr.ev[(size_t)r.e1]));
+    g_last_trace.push_back(r);
+    g_last_trace_ms.push_back(t);
     if (ms) ms[r.cls] += t;
     if (bytes) bytes[r.cls] += r.bytes;
     if (flops) flops[r.cls] += r.flops;
@@ -789,14 +800,22 @@ int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* 
 // ------------------------------------------------------------------------------------------------
 // Learned post-smoother
 
-static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs) {
+// Grow the learned smoother's buffers: forward activations for `pixpairs`
+// pixel-pairs, backward ones too when `backward` (training), and the n x ldk
+// temporaries for `vecs` entries.  (Inference needs only the forward ones.)
+static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs, bool backward) {
   auto& nn = c->nn;
   if (pixpairs > nn.buf.cap) {
     const size_t m = (size_t)pixpairs * 16;
-    float** bufs[] = {&nn.buf.z1, &nn.buf.z2p, &nn.buf.z2m, &nn.buf.h, &nn.buf.gh, &nn.buf.gzp,
-                      &nn.buf.gzm, &nn.buf.gap, &nn.buf.gam, &nn.buf.gz1};
+    float** bufs[] = {&nn.buf.z1, &nn.buf.z2p, &nn.buf.z2m, &nn.buf.h};
     for (float** b : bufs) AL(nn.allocs, b, m);
     nn.buf.cap = pixpairs;
+  }
+  if (backward && pixpairs > nn.bcap) {
+    const size_t m = (size_t)pixpairs * 16;
+    float** bufs[] = {&nn.buf.gh, &nn.buf.gzp, &nn.buf.gzm, &nn.buf.gap, &nn.buf.gam, &nn.buf.gz1};
+    for (float** b : bufs) AL(nn.allocs, b, m);
+    nn.bcap = pixpairs;
   }
   if (vecs > nn.vcap) {
     AL(nn.allocs, &nn.R, (size_t)vecs); AL(nn.allocs, &nn.D, (size_t)vecs); AL(nn.allocs, &nn.X, (size_t)vecs);
@@ -836,7 +855,7 @@ int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
   nn.t = 0;
   // V-cycle use needs the n x ldk temporaries and activations of the largest grid level
   if (c->k > 0 && maxn > 0) {
-    int r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk);
+    int r = nn_ensure(c, maxn * c->ldk, maxn * c->ldk, false);
     if (r) return r;
   }
   nn.ready = true;
@@ -870,7 +889,7 @@ int pasm_nn_apply(pasm_ctx* c, int level, int k, const float* R, float* D) {
   if (!R || !D) return PASM_EINVAL;
   Scope sc(c);
   const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
-  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2, false);
   if (r) return r;
   auto& nn = c->nn;
   r = put_block_f(c, R, nn.R, n, k, ldk2);
@@ -903,7 +922,7 @@ int pasm_nn_loss_grad(pasm_ctx* c, int level, int k, const float* R, double* los
   if (!R) return PASM_EINVAL;
   Scope sc(c);
   const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
-  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2, true);
   if (!r) r = put_block_f(c, R, c->nn.R, n, k, ldk2);
   if (r) return r;
   nn_loss_grad_dev(c, level, k, ldk2);
@@ -920,7 +939,7 @@ int pasm_nn_train(pasm_ctx* c, int level, int k, const float* R, int iters, floa
   if (!R || iters < 0 || !(lr > 0.f)) return PASM_EINVAL;
   Scope sc(c);
   const int n = c->lv[(size_t)level].n, ldk2 = ldk_for(k);
-  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2);
+  r = nn_ensure(c, (int64_t)n * ldk2, (int64_t)n * ldk2, true);
   if (!r) r = put_block_f(c, R, c->nn.R, n, k, ldk2);
   if (r) return r;
   auto& nn = c->nn;
@@ -939,7 +958,7 @@ int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {
   if (c->opts.precision != PASM_MIXED) return PASM_EINVAL;
   Scope sc(c);
   const int n = c->lv[(size_t)level].n;
-  int r = nn_ensure(c, 0, (int64_t)n * c->ldk);
+  int r = nn_ensure(c, 0, (int64_t)n * c->ldk, false);
   if (r) return r;
   c->capture_level = level;
   c->capture_buf = c->nn.Rt;
@@ -956,6 +975,21 @@ int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {
 int pasm_nn_accepted(pasm_ctx* c, int* counts) {
   if (!c || !counts || !c->nn.accepted || c->k < 1) return PASM_ESTATE;
   CK(cudaMemcpy(counts, c->nn.accepted, sizeof(int) * c->k, cudaMemcpyDefault));
+  return PASM_OK;
+}
+
+int pasm_trace_launches(pasm_ctx* c, int max, int* cls, int* rows, float* ms, double* bytes, double* flops,
+                        int* count) {
+  if (!c || !count) return PASM_EINVAL;
+  const int n = (int)g_last_trace.size();
+  *count = n;
+  for (int q = 0; q < n && q < max; ++q) {
+    if (cls) cls[q] = g_last_trace[(size_t)q].cls;
+    if (rows) rows[q] = g_last_trace[(size_t)q].rows;
+    if (ms) ms[q] = g_last_trace_ms[(size_t)q];
+    if (bytes) bytes[q] = g_last_trace[(size_t)q].bytes;
+    if (flops) flops[q] = g_last_trace[(size_t)q].flops;
+  }
   return PASM_OK;
 }
 
