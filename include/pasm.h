@@ -252,6 +252,10 @@ int pasm_nn_capture_residuals(pasm_ctx* ctx, int level, float* R_out);
  * since pasm_init or pasm_nn_setup; counts has k entries (host or device). */
 int pasm_nn_accepted(pasm_ctx* ctx, int* counts);
 
+/* Number of tensor-core tiles of the learned smoother whose completion wait
+ * timed out (their output was left unwritten) since pasm_nn_setup. */
+int pasm_nn_errors(pasm_ctx* ctx, int* count);
+
 /* Bordering products of the correction step for callers that cannot allocate
  * device memory.  The paper has no counterpart to this entry point: it exists
  * for hosts that reserve the whole device heap for their own pool, that must

@@ -52,6 +52,7 @@ class Problem:
     # widths (0 / None = plain Jacobi on that level)
     nn_weights: object = None
     grids: object = None
+    nn_bf16: bool = False          # round layer-2 inputs to bfloat16 (tensor-core path)
 
     def __post_init__(self):
         self.L = len(self.A) - 1
@@ -135,7 +136,7 @@ def learned_sweep(prob: Problem, l: int, f, x):
     nx = prob.grids[l]
     ny = A.shape[0] // nx
     r = f - A @ x
-    d = sm.from_grid(sm.apply(prob.nn_weights, sm.to_grid(r, nx, ny)))
+    d = sm.from_grid(sm.apply(prob.nn_weights, sm.to_grid(r, nx, ny), bf16_layer2=prob.nn_bf16))
     xt = x + d
     rt = f - A @ xt
     ok = np.einsum("ij,ij->j", rt, rt) <= np.einsum("ij,ij->j", r, r)

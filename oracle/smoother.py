@@ -119,13 +119,29 @@ def _branch_back(gy, cache, W1, W2, W3):
     return gW1, gW2, gW3
 
 
-def apply(w, r_grid):
-    """N(r) for images r_grid: (B, ny, nx) -> (B, ny, nx)."""
+def bf16(x):
+    """Round to bfloat16 (8-bit significand), round to nearest even, via float32."""
+    b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def apply(w, r_grid, bf16_layer2: bool = False):
+    """N(r) for images r_grid: (B, ny, nx) -> (B, ny, nx).  With bf16_layer2 the
+    inputs of the second convolution (relu(+-z1) and W2) are rounded to
+    bfloat16 first, as the tensor-core path computes that layer."""
     W1, W2, W3 = unpack(w)
     x = r_grid[..., None]
-    yp, _ = _branch(x, W1, W2, W3)
-    ym, _ = _branch(-x, W1, W2, W3)
-    return 0.5 * (yp - ym)[..., 0]
+    if not bf16_layer2:
+        yp, _ = _branch(x, W1, W2, W3)
+        ym, _ = _branch(-x, W1, W2, W3)
+        return 0.5 * (yp - ym)[..., 0]
+    z1 = conv(x, W1)
+    W2b = bf16(W2)
+    z2p = conv(bf16(np.maximum(z1, 0.0)), W2b)
+    z2m = conv(bf16(np.maximum(-z1, 0.0)), W2b)
+    h = 0.5 * (np.maximum(z2p, 0.0) - np.maximum(z2m, 0.0))
+    return conv(h, W3)[..., 0]
 
 
 def loss_and_grad(w, A, R, nx, ny):

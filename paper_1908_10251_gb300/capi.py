@@ -90,6 +90,7 @@ def load_library():
         "pasm_nn_train": (I, [P, I, I, P, I, ctypes.c_float, P]),
         "pasm_nn_capture_residuals": (I, [P, I, P]),
         "pasm_nn_accepted": (I, [P, P]),
+        "pasm_nn_errors": (I, [P, ctypes.POINTER(I)]),
         "pasm_border_noalloc": (I, [I, P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, I, P, P, P, P, P, P]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
@@ -299,6 +300,12 @@ def pasm_nn_accepted(ctx: Context, k: int):
     out = np.zeros(k, dtype=np.int32)
     _check(load_library().pasm_nn_accepted(ctx.handle, out.ctypes.data), "pasm_nn_accepted")
     return out
+
+
+def pasm_nn_errors(ctx: Context) -> int:
+    n = ctypes.c_int(0)
+    _check(load_library().pasm_nn_errors(ctx.handle, ctypes.byref(n)), "pasm_nn_errors")
+    return n.value
 
 
 def pasm_border_noalloc(n, A_row_ptr, A_col, A_val, M_row_ptr, M_col, M_val, k, X, YA, YM, beta, zeta,

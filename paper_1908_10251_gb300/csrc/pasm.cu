@@ -106,6 +106,7 @@ struct pasm_ctx {
     float *R = nullptr, *D = nullptr, *X = nullptr, *Rt = nullptr, *Es = nullptr, *gD = nullptr;
     double *partial = nullptr, *norms = nullptr, *loss = nullptr;
     int* accepted = nullptr;
+    int* err = nullptr;                      // timed-out tensor-core waits
     std::vector<void*> allocs;
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
@@ -245,7 +246,8 @@ int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
   NNGrid g{nn.nx[l], nn.ny[l], ldk, c->k};
   const float om = (float)c->opts.omega;
   rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, nn.R, ldk);        // r = f - A e
-  nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);                                     // d = N(r)
+  if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.W, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
+  else nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
   nn_add(L, (int64_t)v.n * ldk, cur, nn.D, nn.X);                                 // e + d
   rowop<float>(L, OP_RESID, v.A, nn.X, F, nullptr, nullptr, om, nn.Rt, ldk);      // f - A (e + d)
   nn_column_norms(L, v.n, ldk, nn.R, nn.Rt, nn.partial, nn.norms);
@@ -582,6 +584,7 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
       Ai[(size_t)i * NH + j] = s;
     }
   CK(secular_prepare(NH));
+  CK(nn_tc_prepare());
   AL(c->allocs, &c->lamH, (size_t)NH);
   AL(c->allocs, &c->Q, (size_t)NH * NH);
   AL(c->allocs, &c->AinvH64, (size_t)NH * NH);
@@ -847,6 +850,8 @@ int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
     AL(nn.allocs, &nn.buf.wpart, (size_t)NNBuf::kWgradBlocks * 2304);
     AL(nn.allocs, &nn.buf.wflip2, 2304); AL(nn.allocs, &nn.buf.wflip3, 144);
     AL(nn.allocs, &nn.norms, 2 * 256); AL(nn.allocs, &nn.loss, 1); AL(nn.allocs, &nn.accepted, 256);
+    AL(nn.allocs, &nn.err, 4);
+    CK(cudaMemset(nn.err, 0, sizeof(int) * 4));
   }
   CK(cudaMemcpy(nn.W, weights, sizeof(float) * kNNWeights, cudaMemcpyDefault));
   CK(cudaMemset(nn.m, 0, sizeof(float) * kNNWeights));
@@ -895,7 +900,10 @@ int pasm_nn_apply(pasm_ctx* c, int level, int k, const float* R, float* D) {
   r = put_block_f(c, R, nn.R, n, k, ldk2);
   if (r) return r;
   NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
-  nn_forward(launcher(c), g, nn.buf, nn.W, nn.R, nn.D);
+  if (c->opts.smoother == PASM_LEARNED && nn_tc_supported(ldk2))
+    nn_forward_tc(launcher(c), g, nn.W, nn.R, nn.D, nn.err);
+  else
+    nn_forward(launcher(c), g, nn.buf, nn.W, nn.R, nn.D);
   CK(cudaMemcpy2DAsync(D, sizeof(float) * k, nn.D, sizeof(float) * ldk2, sizeof(float) * k, n, cudaMemcpyDefault,
                        c->s));
   CK(cudaStreamSynchronize(c->s));
@@ -969,6 +977,12 @@ int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {
                        cudaMemcpyDefault, c->s));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_nn_errors(pasm_ctx* c, int* count) {
+  if (!c || !count || !c->nn.err) return PASM_ESTATE;
+  CK(cudaMemcpy(count, c->nn.err, sizeof(int), cudaMemcpyDefault));
   return PASM_OK;
 }
 

@@ -40,4 +40,11 @@ void nn_add(const Launch& L, int64_t total, const float* a, const float* b, floa
 void nn_select(const Launch& L, int n, int ldk, const float* E, const float* D, const float* R, const float* dinv,
                float omega, const double* norms, float* out, int* accepted);
 
+// Fused tensor-core forward (smoother_tc.cu): D = N(R) with layer 2 on tcgen05
+// (bf16 operands, float32 accumulation); needs ldk % 8 == 0.  A timed-out wait
+// increments *err and leaves D unwritten for that tile.
+cudaError_t nn_tc_prepare();
+bool nn_tc_supported(int ldk);
+void nn_forward_tc(const Launch& L, const NNGrid& g, const float* W, const float* R, float* D, int* err);
+
 }  // namespace pasm

@@ -156,3 +156,45 @@ def test_trained_smoother_beats_jacobi_on_held_out_residuals(pg):
     jac_loss = float(np.mean(np.einsum("ij,ij->j", J, J) / np.einsum("ij,ij->j", Rd, Rd)))
     print("held-out loss: learned %.4f, Jacobi %.4f" % (nn_loss, jac_loss))
     assert nn_loss < jac_loss
+
+
+def test_tensor_core_forward_parity(pg):
+    """Fused tcgen05 forward (layer 2 in bf16 on the tensor cores, float32
+    accumulation) against the oracle with the same bf16 rounding of layer 2's
+    inputs; tiles of 14 x 14 pixels x 8 pairs, a grid that is not a multiple of
+    the tile (31 x 31) and a padded pair block (k = 5 of 8)."""
+    w = sm.init_weights(3).astype(np.float32).astype(np.float64) * 2.0
+    H, grids, ctx = make(pg, learned=True, w=w)
+    L = len(H.levels) - 1
+    nx = grids[L]
+    R = np.random.default_rng(4).standard_normal((H.fine.n, 5)).astype(np.float32)
+    D = np.zeros_like(R)
+    pg.pasm_nn_apply(ctx, L, R, D)
+    ref = sm.from_grid(sm.apply(w, sm.to_grid(R.astype(np.float64), nx, nx), bf16_layer2=True))
+    err = np.abs(D - ref) / np.abs(ref).max()
+    assert err.max() < 1e-2 and np.median(err) < 1e-4, (err.max(), np.median(err))
+    plain = sm.from_grid(sm.apply(w, sm.to_grid(R.astype(np.float64), nx, nx)))
+    assert rel(D, plain) < 5e-2                      # bf16 changes the result by well under 5 %
+    assert pg.pasm_nn_errors(ctx) == 0
+
+
+def test_vcycle_with_tensor_core_smoother(pg):
+    """The V-cycle with the tcgen05 learned step (trained-like weights, so the
+    step is accepted) against the oracle's cycle with bf16 rounding of layer 2."""
+    H0, g0, ctx0 = make(pg)
+    L = len(H0.levels) - 1
+    k = 8
+    pg.pasm_init(ctx0, k, 0.0)
+    R = np.zeros((H0.fine.n, k), dtype=np.float32)
+    pg.pasm_nn_capture_residuals(ctx0, L, R)
+    pg.pasm_nn_train(ctx0, L, R, 200, 3e-3)
+    w = pg.pasm_nn_get_weights(ctx0).astype(np.float64)
+    H, grids, ctx = make(pg, learned=True, w=w)
+    prob = oracle.Problem.from_hierarchy(H, nn_weights=w, grids=grids, nn_bf16=True)
+    lam, U = oracle.initial_state(prob, k)
+    pg.pasm_init(ctx, k, 0.0, lam, U)
+    Uh = np.zeros_like(U)
+    pg.pasm_bvp(ctx, lam, U, Uh)
+    ref = op.bvp_solve(prob, lam, U)
+    assert rel(Uh, ref) < 1e-4
+    assert pg.pasm_nn_accepted(ctx, k).sum() > 0

@@ -109,3 +109,9 @@ def test_zero_network_learned_sweep_is_jacobi_or_identity():
     rng = np.random.default_rng(0)
     f = rng.standard_normal((H.fine.n, 2)); x = rng.standard_normal((H.fine.n, 2))
     assert np.array_equal(op.learned_sweep(prob, prob.L, f, x), x)
+
+
+def test_bf16_rounding_matches_torch():
+    x = np.random.default_rng(9).standard_normal(1000) * 10.0 ** np.random.default_rng(10).integers(-5, 5, 1000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(sm.bf16(x), ref)
