@@ -286,6 +286,31 @@ int pasm_border_noalloc(int n, const int32_t* A_row_ptr, const int32_t* A_col, c
                         int64_t M_nnz, int k, const double* X, double* YA, double* YM, double* beta,
                         double* zeta, void* stream);
 
+/* ---- Batches of independent problems of uneven size (several meshes, several
+ * k per mesh).  Distinct problems, like the pairs of Algorithm 2, never
+ * exchange data; the batch steps them together, each on its own stream, so
+ * that the correction steps of small problems overlap on the GPU. */
+typedef struct pasm_batch pasm_batch;
+
+/* One context per problem p: n_levels[p] levels, A[p], M[p] arrays of
+ * n_levels[p] matrices, P[p] of n_levels[p] - 1 (see pasm_setup); opts shared
+ * (NULL = defaults); stream = the caller's stream the batch orders itself
+ * after.  Errors as pasm_setup. */
+int pasm_batch_setup(pasm_batch** out, int n_problems, const int* n_levels, const pasm_csr* const* A,
+                     const pasm_csr* const* M, const pasm_csr* const* P, const pasm_opts* opts, void* stream);
+
+/* Solve every problem p for its k[p] smallest pairs from its coarse start:
+ * correction steps of all unfinished problems are launched together until
+ * every pair is frozen or opts.max_steps rounds.  Outputs per problem (each
+ * array of pointers may be NULL; entries host or device): lambda_out[p] (k[p]),
+ * U_out[p] (n_p x k[p]), steps_out[p], status_out[p]; *batch_steps = rounds.
+ * Returns PASM_ENOTCONV if any pair is still active (outputs written). */
+int pasm_batch_solve(pasm_batch* b, const int* k, double tol, double* const* lambda_out, double* const* U_out,
+                     int* const* steps_out, int* const* status_out, int* batch_steps);
+
+/* Release the batch and every context in it.  NULL is a no-op. */
+void pasm_batch_destroy(pasm_batch* b);
+
 /* Release the context and all its device memory.  NULL is a no-op. */
 void pasm_destroy(pasm_ctx* ctx);
 

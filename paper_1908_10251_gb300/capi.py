@@ -92,6 +92,9 @@ def load_library():
         "pasm_nn_accepted": (I, [P, P]),
         "pasm_nn_errors": (I, [P, ctypes.POINTER(I)]),
         "pasm_border_noalloc": (I, [I, P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, I, P, P, P, P, P, P]),
+        "pasm_batch_setup": (I, [ctypes.POINTER(P), I, P, P, P, P, ctypes.POINTER(pasm_opts), P]),
+        "pasm_batch_solve": (I, [P, P, ctypes.c_double, P, P, P, P, ctypes.POINTER(I)]),
+        "pasm_batch_destroy": (None, [P]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
     }
@@ -317,6 +320,68 @@ def pasm_border_noalloc(n, A_row_ptr, A_col, A_val, M_row_ptr, M_col, M_val, k, 
         else A_val.size, _ptr(M_row_ptr, np.int32), _ptr(M_col, np.int32), _ptr(M_val),
         M_val.numel() if hasattr(M_val, "numel") else M_val.size, k, _ptr(X), _ptr(YA), _ptr(YM), _ptr(beta),
         _ptr(zeta), stream), "pasm_border_noalloc")
+
+
+class Batch:
+    """Owns a pasm_batch* and the host CSR copies of every problem."""
+
+    def __init__(self, handle, keep, sizes):
+        self.handle = handle
+        self._keep = keep
+        self.sizes = sizes
+
+    def __del__(self):
+        try:
+            pasm_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def pasm_batch_setup(problems, opts=None, stream=None) -> Batch:
+    """problems: list of (A_levels, M_levels, P_levels) (coarsest first)."""
+    lib = load_library()
+    n = len(problems)
+    keep, aptr, mptr, pptr, nlev, sizes = [], [], [], [], [], []
+    for A, M, P in problems:
+        L = len(A)
+        arrA = (pasm_csr * L)(); arrM = (pasm_csr * L)(); arrP = (pasm_csr * max(L - 1, 1))()
+        for l in range(L):
+            arrA[l], k1 = _csr(A[l]); arrM[l], k2 = _csr(M[l]); keep += [k1, k2]
+        for l in range(L - 1):
+            arrP[l], k3 = _csr(P[l]); keep.append(k3)
+        keep += [arrA, arrM, arrP]
+        aptr.append(ctypes.addressof(arrA)); mptr.append(ctypes.addressof(arrM)); pptr.append(ctypes.addressof(arrP))
+        nlev.append(L)
+        sizes.append(A[-1].shape[0])
+    AP = (ctypes.c_void_p * n)(*aptr); MP = (ctypes.c_void_p * n)(*mptr); PP = (ctypes.c_void_p * n)(*pptr)
+    NL = (ctypes.c_int * n)(*nlev)
+    keep += [AP, MP, PP, NL]
+    h = ctypes.c_void_p()
+    o = opts if opts is not None else pasm_default_opts()
+    _check(lib.pasm_batch_setup(ctypes.byref(h), n, NL, AP, MP, PP, ctypes.byref(o), stream), "pasm_batch_setup")
+    return Batch(h, keep, sizes)
+
+
+def pasm_batch_solve(batch: Batch, ks, tol: float):
+    """Returns (code, lams, Us, steps, statuses, rounds) with host numpy outputs per problem."""
+    lib = load_library()
+    n = len(batch.sizes)
+    lams = [np.zeros(k) for k in ks]
+    Us = [np.zeros((nf, k)) for nf, k in zip(batch.sizes, ks)]
+    steps = [np.zeros(k, dtype=np.int32) for k in ks]
+    stats = [np.zeros(k, dtype=np.int32) for k in ks]
+    arr = lambda xs: (ctypes.c_void_p * n)(*[x.ctypes.data for x in xs])  # noqa: E731
+    K = (ctypes.c_int * n)(*ks)
+    rounds = ctypes.c_int(0)
+    code = _check(lib.pasm_batch_solve(batch.handle, K, tol, arr(lams), arr(Us), arr(steps), arr(stats),
+                                       ctypes.byref(rounds)), "pasm_batch_solve", allow=(PASM_ENOTCONV,))
+    return code, lams, Us, steps, stats, rounds.value
+
+
+def pasm_batch_destroy(batch: Batch):
+    if batch.handle is not None and batch.handle.value:
+        load_library().pasm_batch_destroy(batch.handle)
+    batch.handle = ctypes.c_void_p()
 
 
 def pasm_destroy(ctx: Context):

@@ -703,6 +703,15 @@ int pasm_step(pasm_ctx* c, int* n_active) {
   return PASM_OK;
 }
 
+// Wait for the context's queued work and return the active-pair count the
+// last step left in pinned memory (used by the batch driver).
+int pasm_ctx_wait_active(pasm_ctx* c, int* n_active) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  CK(cudaStreamSynchronize(c->s));
+  *n_active = *c->h_nact;
+  return PASM_OK;
+}
+
 int pasm_get(pasm_ctx* c, double* lambda, double* U, int* steps, int* status) {
   if (!c || !c->initialized) return PASM_ESTATE;
   Scope sc(c);

@@ -342,3 +342,15 @@ def test_frozen_pairs_do_not_change():
     lam, U, steps, hist = oracle.solve(prob, 2, tol=1e-6, max_steps=30, history=True)
     lam2, U2, steps2, _ = oracle.solve(prob, 2, tol=1e-6, max_steps=60)
     assert np.array_equal(steps, steps2) and np.array_equal(lam, lam2)
+
+
+def test_variable_coefficient_pairs_match_reference():
+    """-div(kappa grad u) = lambda u with kappa = exp(g) on a Galerkin hierarchy:
+    the first converged PASM eigenvalues equal the reference eigenvalues
+    (ARPACK shift-invert of the finest pencil) to 1e-12."""
+    from oracle.reference import smallest_eigenvalues
+    H = mg.build_hierarchy(2, 64, 8, kappa=mg.gaussian_log_field(64, 1001))
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U, steps, _ = oracle.solve(prob, 3, tol=1e-13, max_steps=60)
+    ref = smallest_eigenvalues(H.fine.A, H.fine.M, 3)
+    assert np.allclose(lam, ref, rtol=1e-12)
