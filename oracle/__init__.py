@@ -18,6 +18,6 @@ against itself.
 """
 from .pasm import (  # noqa: F401
     Problem, coarse_eigenpairs, jacobi, vcycle, bvp_solve, bordering,
-    augmented_eigenproblem, correction, initial_state, solve,
+    augmented_eigenproblem, correction, initial_state, initial_state_nested, solve,
     SCORE_A, SCORE_B,
 )

@@ -99,6 +99,25 @@ def initial_state(prob: Problem, k: int):
     return lam[:k].copy(), np.asarray(U)
 
 
+def sub_problem(prob: Problem, l: int) -> Problem:
+    """The hierarchy truncated at level l (V_H = level 0 stays the coarse space)."""
+    return Problem(prob.A[:l + 1], prob.M[:l + 1], prob.P[:l], omega=prob.omega, nu_pre=prob.nu_pre,
+                   nu_post=prob.nu_post, cycles=prob.cycles, score=prob.score, nn_weights=prob.nn_weights,
+                   grids=None if prob.grids is None else prob.grids[:l + 1], nn_bf16=prob.nn_bf16)
+
+
+def initial_state_nested(prob: Problem, k: int):
+    """Algorithm 2 with h_1 = H: step 1 on V_H, then step 2(A) -- on every
+    intermediate level one correction step (varpi = 1, the choice the paper
+    recommends for the intermediate levels) started from the prolongated
+    pairs of the level below -- and prolongation to the finest level."""
+    lam, U = initial_state(sub_problem(prob, 0), k)      # pairs on V_H (u = q / sqrt(Lambda))
+    for l in range(1, prob.L):
+        U = prob.P[l - 1] @ U
+        lam, U, _ = correction(sub_problem(prob, l), lam, U)
+    return lam, prob.P[prob.L - 1] @ U if prob.L >= 1 else U
+
+
 # ----------------------------------------------------------------------------- Algorithm 1, step 1
 
 def jacobi(A, dinv, f, x, omega, nu):
@@ -228,12 +247,12 @@ def correction(prob: Problem, lam, U, active=None):
 # ----------------------------------------------------------------------------- Algorithm 2, step 2(B)
 
 def solve(prob: Problem, k: int, tol: float = 1e-10, max_steps: int = 100,
-          lam0=None, U0=None, history: bool = False):
+          lam0=None, U0=None, history: bool = False, nested: bool = False):
     """Correction steps on the finest level until every pair is frozen
     (|d lambda| / lambda < tol) or max_steps.  Returns (lam, U, steps, hist)
     with steps = per-pair number of correction steps taken."""
     if lam0 is None:
-        lam, U = initial_state(prob, k)
+        lam, U = initial_state_nested(prob, k) if nested else initial_state(prob, k)
     else:
         lam, U = np.array(lam0, dtype=np.float64), np.array(U0, dtype=np.float64)
     active = np.ones(k, dtype=bool)

@@ -648,6 +648,24 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
     r = put_lambda(c, lambda0, c->lam);
     if (!r) r = put_block(c, U0, c->U, nf);
     if (r) return r;
+  } else if (c->opts.init == PASM_INIT_NESTED && c->nlev >= 3) {
+    // Algorithm 2 with h_1 = H: pairs on V_H, then one correction step on every
+    // intermediate level l (step 2(A), varpi = 1), each started from the
+    // prolongated pairs of level l - 1; finally prolongation to the finest level.
+    const size_t ldk = (size_t)c->ldk;
+    coarse_init(L, c->NH, k, c->Q, c->lamH, c->uH, c->lam, c->ldk);
+    r = set_active(c, c->active, c->steps, c->status);
+    if (r) return r;
+    const double* src = c->uH;
+    for (int l = 1; l < c->nlev; ++l) {
+      rowop<double>(L, OP_SPMM, c->lv[l].P, src, nullptr, nullptr, nullptr, 0.0, c->YM, c->ldk);
+      CK(cudaMemcpyAsync(c->U, c->YM, sizeof(double) * (size_t)c->lv[l].n * ldk, cudaMemcpyDeviceToDevice, c->s));
+      if (l == c->nlev - 1) break;
+      bvp(c, l, c->lam, c->U, c->X);
+      PairState ps{c->lam, c->active, c->steps, c->status, c->U, 0.0};
+      augmented(c, l, c->X, ps);
+      src = c->U;
+    }
   } else {
     // u_i = P_c q_i / sqrt(Lambda_i), lambda_i = Lambda_i
     double* w = (c->nlev == 1) ? c->U : c->uH;

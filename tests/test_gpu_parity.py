@@ -278,3 +278,18 @@ def test_device_pointers_and_stream(pg):
     torch.cuda.synchronize()
     assert np.allclose(lg.cpu().numpy(), lo, rtol=1e-10)
     assert colrel(Ug.cpu().numpy(), Uo) < 1e-8
+
+
+def test_nested_initial_state(pg):
+    """Algorithm 2 step 2(A): one correction step on every intermediate level
+    before the finest, GPU vs oracle (h = 1/64, H = 1/8, 4 grids)."""
+    H = mg.build_hierarchy(2, 64, 8)
+    ctx = setup_ctx(pg, H, init=1)
+    prob = oracle.Problem.from_hierarchy(H)
+    k = 6
+    pg.pasm_init(ctx, k, 1e-10)
+    lam, U, steps, status = get_state(pg, ctx, H.fine.n, k)
+    lo, Uo = oracle.initial_state_nested(prob, k)
+    assert np.allclose(lam, lo, rtol=1e-10)
+    assert colrel(align(U, Uo), Uo) < 1e-8
+    assert np.all(steps == 0) and np.all(status == 0)

@@ -354,3 +354,22 @@ def test_variable_coefficient_pairs_match_reference():
     lam, U, steps, _ = oracle.solve(prob, 3, tol=1e-13, max_steps=60)
     ref = smallest_eigenvalues(H.fine.A, H.fine.M, 3)
     assert np.allclose(lam, ref, rtol=1e-12)
+
+
+def test_nested_start_is_upper_bound_and_closer():
+    """Algorithm 2 step 2(A) (one correction per intermediate level): the
+    starting eigenvalues on the finest level are Ritz values of a subspace of
+    V_h, hence upper bounds of the discrete eigenvalues (min-max), and closer
+    to them than the prolongated coarse start."""
+    H = mg.build_hierarchy(2, 64, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    k = 5
+    lam_ref, _ = dense_pairs(H.fine, k)
+    lc, Uc = oracle.initial_state(prob, k)
+    ln, Un = oracle.initial_state_nested(prob, k)
+    assert np.all(ln >= lam_ref * (1 - 1e-12))
+    assert np.all(ln - lam_ref < 0.2 * (lc - lam_ref))
+    A, M = H.fine.A, H.fine.M
+    for i in range(k):
+        u = Un[:, i]
+        assert (u @ (A @ u)) / (u @ (M @ u)) == pytest.approx(ln[i], rel=1e-10)
