@@ -74,13 +74,26 @@ def test_fullsize_fp64_steps_match_oracle_history(pg, square1024):
     pg.pasm_destroy(ctx)
 
 
+def cluster_err(lam, ref_all):
+    """relative distance of each lam_i to the nearest reference eigenvalue of
+    pair i's cluster (consecutive reference values closer than 1e-4 relative)"""
+    cid = np.concatenate([[0], np.cumsum(np.diff(ref_all) / ref_all[1:] > 1e-4)])
+    out = np.empty(len(lam))
+    for i, v in enumerate(lam):
+        mem = ref_all[cid == cid[i]]
+        out[i] = np.min(np.abs(v - mem) / mem)
+    return out
+
+
 def test_fullsize_mixed_converges_to_reference(pg, square1024):
     """Mixed precision at full size: every pair the oracle drives to 1e-9 of
-    the ARPACK eigenvalues gets there on the GPU too, within 40 steps."""
-    ref = np.loadtxt(os.path.join(GOLDEN, "square_h1024_k72.txt"))[:64]
+    the ARPACK eigenvalues (of its own near-degenerate cluster: pairs 15/16 are
+    split by 1.7e-11, 20/21 by 3.2e-9) gets there on the GPU too, within 40
+    steps."""
+    ref_all = np.loadtxt(os.path.join(GOLDEN, "square_h1024_k72.txt"))
     with open(os.path.join(GOLDEN, "square_h1024_H16_k64_history.json")) as f:
         hist = np.array(json.load(f)["history"])
-    conv = np.where((np.abs(hist - ref) / ref <= 1e-9).any(axis=0))[0]
+    conv = np.where(np.array([cluster_err(row, ref_all) for row in hist]).min(axis=0) <= 1e-9)[0]
     assert len(conv) >= 10
     ctx = setup_ctx(pg, square1024, precision=1)
     k = 64
@@ -90,8 +103,8 @@ def test_fullsize_mixed_converges_to_reference(pg, square1024):
     for _ in range(40):
         pg.pasm_step(ctx)
         pg.pasm_get(ctx, lam)
-        best = np.minimum(best, np.abs(lam - ref) / ref)
-    assert np.all(best[conv] <= 1e-9), best[conv]
+        best = np.minimum(best, cluster_err(lam, ref_all))
+    assert np.all(best[conv] <= 1e-9), (conv, best[conv])
     pg.pasm_destroy(ctx)
 
 
