@@ -47,7 +47,8 @@ typedef enum {
   PASM_EDEGENERATE = 6, /* bordered mass matrix singular for a pair (u~ in V_H) */
   PASM_ENAN = 7,        /* a NaN/Inf appeared in a pair                         */
   PASM_ESTATE = 8,      /* call out of order (e.g. pasm_step before pasm_init)  */
-  PASM_ENOTPD = 9       /* coarse A_H or M_H not symmetric positive definite    */
+  PASM_ENOTPD = 9,      /* coarse A_H or M_H not symmetric positive definite    */
+  PASM_ETIMEOUT = 10    /* a bounded device wait gave up (tensor-core kernel)   */
 } pasm_status;
 
 /* Per-pair status values written by pasm_get / pasm_solve. */
@@ -62,6 +63,7 @@ enum { PASM_FP64 = 0, PASM_MIXED = 1 };           /* precision of the V-cycles  
 enum { PASM_SCORE_A = 0, PASM_SCORE_B = 1 };      /* normalisation in the score  */
 enum { PASM_INIT_COARSE = 0, PASM_INIT_NESTED = 1 };
 enum { PASM_JACOBI = 0, PASM_LEARNED = 1 };       /* post-smoother               */
+enum { PASM_PROJ_TENSOR = 0, PASM_PROJ_FP64 = 1 };  /* coarse projection product */
 
 /* A sparse matrix in CSR form: n_rows x n_cols, nnz entries, 32-bit indices,
  * float64 values, column indices ascending within each row. */
@@ -96,6 +98,12 @@ typedef struct {
                           pasm_nn_setup the first post-smoothing sweep is the
                           learned step with a per-pair Jacobi fallback (mixed
                           precision only) [PASM_JACOBI]                        */
+  int projection;      /* PASM_PROJ_TENSOR: the dense coarse products Q^T b,
+                          Q^T c and Q g run on the tensor cores (tcgen05) in
+                          exact digit planes, added exactly and rounded once
+                          to float64 (error about 2^-56 N_H max|Q| max|b|);
+                          PASM_PROJ_FP64: float64 CUDA-core products
+                          [PASM_PROJ_TENSOR]                                    */
 } pasm_opts;
 
 typedef struct pasm_ctx pasm_ctx;
@@ -134,7 +142,8 @@ int pasm_step(pasm_ctx* ctx, int* n_active);
 
 /* Copy the current state out: lambda (k), U (n x k), steps (k, correction
  * steps taken per pair), status (k, PASM_PAIR_*).  Any pointer may be NULL.
- * Synchronises the stream. */
+ * Synchronises the stream.  Returns PASM_ETIMEOUT (outputs still written) if a
+ * tensor-core projection has ever given up a bounded wait in this context. */
 int pasm_get(pasm_ctx* ctx, double* lambda, double* U, int* steps, int* status);
 
 /* pasm_init + pasm_step until no pair is active or opts.max_steps, then
@@ -156,6 +165,20 @@ int pasm_bvp(pasm_ctx* ctx, const double* lambda, const double* U, double* Uhat)
  * the Ritz roots are searched around.  Needs pasm_init with the same k. */
 int pasm_augmented(pasm_ctx* ctx, const double* lambda_prev, const double* Uhat,
                    double* lambda_out, double* U_out, double* beta, double* zeta);
+
+/* The projection of Algorithm 1 step 2 onto the coarse eigenbasis alone:
+ * bq = Q^T b and cq = Q^T c for the k columns of b and c (N_H x k row-major,
+ * host or device; b = P_c^T A u~ and c = P_c^T M u~ are the bordering vectors
+ * of the bordered matrix form in Section 3.1, and Q is the M_H-orthonormal
+ * coarse eigenbasis of pasm_coarse_eigs).  The product follows
+ * opts.projection.  Needs pasm_init (for k); uses the coarse scratch of a
+ * step.  Errors: PASM_ESTATE, PASM_EINVAL (NULL pointer), PASM_ETIMEOUT (a
+ * tensor-core wait gave up; outputs then incomplete). */
+int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, double* cq);
+
+/* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else
+ * PASM_PROJ_FP64. */
+int pasm_projection_kind(pasm_ctx* ctx, int* kind);
 
 /* The coarse eigendecomposition computed at setup: Lambda_H (N_H, ascending)
  * and Q (N_H x N_H row-major, column j = eigenvector j, Q^T M_H Q = I); host
@@ -188,6 +211,7 @@ enum {
   PASM_KC_COUNT,        /* active-pair count                                      */
   PASM_KC_CAST,         /* precision conversion                                   */
   PASM_KC_NN,           /* learned smoother (convolutions, training, fallback)    */
+  PASM_KC_PROJ,         /* coarse projections Q^T b, Q^T c, Q g on tensor cores   */
   PASM_KC_N
 };
 

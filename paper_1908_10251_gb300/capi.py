@@ -20,12 +20,13 @@ LIB_PATH = os.path.join(HERE, "libpasm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pasm.h")
 
 PASM_OK, PASM_EINVAL, PASM_EK_TOO_BIG, PASM_ENOMEM, PASM_ECUDA = 0, 1, 2, 3, 4
-PASM_ENOTCONV, PASM_EDEGENERATE, PASM_ENAN, PASM_ESTATE, PASM_ENOTPD = 5, 6, 7, 8, 9
+PASM_ENOTCONV, PASM_EDEGENERATE, PASM_ENAN, PASM_ESTATE, PASM_ENOTPD, PASM_ETIMEOUT = 5, 6, 7, 8, 9, 10
 PASM_PAIR_ACTIVE, PASM_PAIR_CONVERGED, PASM_PAIR_DEGENERATE, PASM_PAIR_NAN = 0, 1, 2, 3
 PASM_FP64, PASM_MIXED = 0, 1
 PASM_SCORE_A, PASM_SCORE_B = 0, 1
 PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
 PASM_JACOBI, PASM_LEARNED = 0, 1
+PASM_PROJ_TENSOR, PASM_PROJ_FP64 = 0, 1
 NN_WEIGHTS = 2592
 
 
@@ -38,7 +39,7 @@ class pasm_opts(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("cycles_per_step", ctypes.c_int), ("max_steps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("projection", ctypes.c_int)]
 
 
 class PasmError(RuntimeError):
@@ -77,6 +78,8 @@ def load_library():
         "pasm_bvp": (I, [P, P, P, P]),
         "pasm_augmented": (I, [P, P, P, P, P, P, P]),
         "pasm_coarse_eigs": (I, [P, P, P]),
+        "pasm_project": (I, [P, P, P, P, P]),
+        "pasm_projection_kind": (I, [P, ctypes.POINTER(I)]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
@@ -210,6 +213,17 @@ def pasm_augmented(ctx: Context, lam_prev, Uhat, lambda_out=None, U_out=None, be
                                          _ptr(beta), _ptr(zeta)), "pasm_augmented")
 
 
+def pasm_project(ctx: Context, b, c, bq, cq):
+    """bq = Q^T b, cq = Q^T c (N_H x k each, host or device)."""
+    _check(load_library().pasm_project(ctx.handle, _ptr(b), _ptr(c), _ptr(bq), _ptr(cq)), "pasm_project")
+
+
+def pasm_projection_kind(ctx: Context) -> int:
+    kind = ctypes.c_int(-1)
+    _check(load_library().pasm_projection_kind(ctx.handle, ctypes.byref(kind)), "pasm_projection_kind")
+    return kind.value
+
+
 def pasm_sizes(ctx: Context):
     n = ctypes.c_int64(); nh = ctypes.c_int32(); nl = ctypes.c_int32(); k = ctypes.c_int32()
     _check(load_library().pasm_sizes(ctx.handle, ctypes.byref(n), ctypes.byref(nh), ctypes.byref(nl),
@@ -231,7 +245,7 @@ def pasm_last_launches(ctx: Context) -> int:
     return n.value
 
 
-PASM_KC_N = 17
+PASM_KC_N = 18
 
 
 def pasm_trace_step(ctx: Context):

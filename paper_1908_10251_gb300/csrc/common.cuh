@@ -53,3 +53,21 @@ struct RowMap {
   int tpr;   // threads per row (power of two, <= 32)
   int rpb;   // rows per block
 };
+
+// Allow `func` up to `need` bytes of dynamic shared memory on the current
+// device.  The limit is set to the device's opt-in maximum less the kernel's
+// static shared memory, so it never drops below what an earlier context of a
+// larger size needs; fails with cudaErrorInvalidValue if `need` exceeds it.
+inline cudaError_t allow_dynamic_smem(const void* func, size_t need) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  const size_t cap = (size_t)optin - fa.sharedSizeBytes;
+  if (need > cap) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+}

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace pasm {
 
 // Device CSR matrix with float64 values and an optional float32 shadow.
@@ -22,7 +24,7 @@ template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
 // Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
 enum KernelClass {
   KC_JACOBI = 0, KC_JACOBI0, KC_RESID, KC_SPMM, KC_PROLONG, KC_DENSE, KC_OUTER_RHS, KC_OUTER_RES, KC_AXPY,
-  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_N
+  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_PROJ, KC_N
 };
 
 // Host-side event recorder (defined in pasm.cu); null when not tracing.
@@ -126,6 +128,41 @@ void update_pairs(const Launch& L, const DCsr& P, const double* W, const double*
 // Same with P = identity (single-level hierarchy): U = alpha X + W.
 void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
                            const int* upd, double* U, int ldk);
+
+// ----------------------------------------------------------------------------------------------
+// Float64-accurate dense product C = A B on the tensor cores (proj_tc.cu).
+// A (m x K) is split once into S = 8 signed 7-bit digit planes per row
+// (error-free slicing in the manner of Ozaki, Ogita, Oishi and Rump), B (K x n)
+// per call per column; the digit-plane products run as bf16 x bf16 -> f32
+// tcgen05 MMAs over chunks of 32 inner indices, whose integer sums are exact in
+// float32; they are added exactly in 64-bit integers and rounded once.
+struct ProjPlan {
+  int beta = 0, S = 0;  // digit width and digits per operand
+};
+struct SplitMat {
+  int m = 0, K = 0, Kpad = 0, mtiles = 0;
+  ProjPlan plan;
+  const uint16_t* planes = nullptr;  // bf16 [mtiles][S][Kpad/8][16][8][8] (tensor-core operand layout)
+  const int* rexp = nullptr;          // m row exponents: |A[i][j]| < 2^rexp[i]
+};
+// Plan for inner dimension K (false if K is too large for the exact sums).
+bool proj_plan(int K, ProjPlan& plan);
+// Split the row-major m x K host matrix A per the plan: planes (bf16 bits) and
+// row exponents, in the layout SplitMat describes.
+void proj_split_host(const double* A, int m, int K, const ProjPlan& plan, int& Kpad, int& mtiles,
+                     std::vector<uint16_t>& planes, std::vector<int>& rexp);
+// Device scratch of proj_tc for m rows and up to ncols_max columns: 64-bit
+// words of the integer sums and per-tile tickets, both zero-initialised once
+// (each call leaves them zero).
+size_t proj_scratch_words(int m, int ncols_max);
+size_t proj_tickets(int m, int ncols_max);
+cudaError_t proj_tc_prepare();
+// C = A B for ncols output columns: column c < ldk comes from B0/C0 column c,
+// column c >= ldk from B1/C1 column c - ldk (B1, C1 unused when ncols <= ldk).
+// B0, B1, C0, C1 are K x ldk and m x ldk row-major.  err counts bounded waits
+// that gave up (the affected chunk then adds nothing to its tile).
+void proj_tc(const Launch& L, const SplitMat& A, const double* B0, const double* B1, double* C0, double* C1,
+             int ldk, int ncols, unsigned long long* hl, unsigned int* tickets, int* err);
 
 // *out = number of nonzero entries of active[0..k)
 void count_active(const Launch& L, const int* active, int k, int* out);

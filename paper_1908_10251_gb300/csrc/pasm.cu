@@ -111,6 +111,12 @@ struct pasm_ctx {
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
   float* capture_buf = nullptr;
+  // float64-accurate coarse projections on the tensor cores: Q^T (b, c) and Q g
+  bool proj_tc = false;
+  SplitMat projQT, projQ;
+  int* proj_err = nullptr;                 // timed-out tensor-core waits of the projection kernel
+  unsigned long long* proj_hl = nullptr;   // integer sums of the projection (k-dependent scratch)
+  unsigned int* proj_tickets = nullptr;
   int launches = 0;
   int last_launches = 0;
   bool initialized = false;
@@ -334,6 +340,17 @@ struct PairState {
   double tol;
 };
 
+// Projection onto the coarse eigenbasis, b' = Q^T b and c' = Q^T c for all
+// columns (tensor cores, float64-accurate, or float64 CUDA cores).
+void project_bc(pasm_ctx* c, const Launch& L, const double* b, const double* cc, double* bq, double* cq) {
+  if (c->proj_tc) {
+    proj_tc(L, c->projQT, b, cc, bq, cq, c->ldk, 2 * c->ldk, c->proj_hl, c->proj_tickets, c->proj_err);
+  } else {
+    dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, b, bq, c->ldk);
+    dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, cc, cq, c->ldk);
+  }
+}
+
 // Algorithm 1 step 2 on level lt for the columns of X: bordering, projection,
 // secular solve and selection, and the update Uout = alpha X + P_c u_H.
 void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
@@ -350,8 +367,7 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
     sa = c->lv[l - 1].BA;
     sm = c->lv[l - 1].BM;
   }
-  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, sa, c->bq, ldk);
-  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, sm, c->cq, ldk);
+  project_bc(c, L, sa, sm, c->bq, c->cq);
   SecularArgs a;
   a.NH = c->NH; a.k = c->k; a.ldk = ldk;
   a.lamH = c->lamH; a.bq = c->bq; a.cq = c->cq;
@@ -360,7 +376,10 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   a.active = ps.active; a.upd = c->upd; a.steps = ps.steps; a.status = ps.status;
   a.tol = ps.tol; a.score_norm = c->opts.score_norm; a.window = 3; a.diag = c->diag;
   secular_select(L, a);
-  dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, false, c->g, c->uH, ldk);
+  if (c->proj_tc)
+    proj_tc(L, c->projQ, c->g, nullptr, c->uH, nullptr, ldk, ldk, c->proj_hl, c->proj_tickets, c->proj_err);
+  else
+    dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, false, c->g, c->uH, ldk);
   const double* w = c->uH;
   for (int l = 1; l < lt; ++l) {
     rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
@@ -420,6 +439,13 @@ int alloc_k(pasm_ctx* c, int k) {
   AL(K, &c->active, ldk); AL(K, &c->upd, ldk); AL(K, &c->steps, ldk); AL(K, &c->status, ldk);
   AL(K, &c->active2, ldk); AL(K, &c->steps2, ldk); AL(K, &c->status2, ldk);
   AL(K, &c->nact, 1); AL(K, &c->diag, 8);
+  if (c->proj_tc) {
+    const size_t words = proj_scratch_words(c->NH, 2 * ldk), tickets = proj_tickets(c->NH, 2 * ldk);
+    AL(K, &c->proj_hl, words); AL(K, &c->proj_tickets, tickets);
+    CK(cudaMemsetAsync(c->proj_hl, 0, sizeof(unsigned long long) * words, c->s));
+    CK(cudaMemsetAsync(c->proj_tickets, 0, sizeof(unsigned int) * tickets, c->s));
+  }
+  for (double* z : {c->bq, c->cq, c->g, c->uH}) CK(cudaMemsetAsync(z, 0, sizeof(double) * nh, c->s));
   CK(cudaMemsetAsync(c->U, 0, sizeof(double) * n * ldk, c->s));
   CK(cudaMemsetAsync(c->X, 0, sizeof(double) * n * ldk, c->s));
   CK(cudaMemsetAsync(c->diag, 0, sizeof(int) * 8, c->s));
@@ -473,6 +499,7 @@ void pasm_default_opts(pasm_opts* o) {
   o->init = PASM_INIT_COARSE;
   o->use_graph = 1;
   o->smoother = PASM_JACOBI;
+  o->projection = PASM_PROJ_TENSOR;
 }
 
 const char* pasm_strerror(int st) {
@@ -487,6 +514,7 @@ const char* pasm_strerror(int st) {
     case PASM_ENAN: return "NaN or Inf in a pair";
     case PASM_ESTATE: return "call out of order";
     case PASM_ENOTPD: return "coarse matrix not symmetric positive definite";
+    case PASM_ETIMEOUT: return "a bounded device wait gave up";
     default: return "unknown status";
   }
 }
@@ -596,6 +624,36 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
     AL(c->allocs, &c->AinvH32, (size_t)NH * NH);
     CK(cudaMemcpy(c->AinvH32, af.data(), sizeof(float) * NH * NH, cudaMemcpyHostToDevice));
   }
+  AL(c->allocs, &c->proj_err, 1);
+  CK(cudaMemset(c->proj_err, 0, sizeof(int)));
+  ProjPlan plan;
+  if (c->opts.projection == PASM_PROJ_TENSOR && proj_plan(NH, plan)) {
+    // digit planes of Q^T (for b' = Q^T b, c' = Q^T c) and of Q (for u_H = Q g)
+    std::vector<double> QT((size_t)NH * NH);
+    for (int i = 0; i < NH; ++i)
+      for (int j = 0; j < NH; ++j) QT[(size_t)i * NH + j] = c->h_Q[(size_t)j * NH + i];
+    SplitMat* dst[2] = {&c->projQT, &c->projQ};
+    const double* srcm[2] = {QT.data(), c->h_Q.data()};
+    for (int q = 0; q < 2; ++q) {
+      std::vector<uint16_t> planes;
+      std::vector<int> rexp;
+      SplitMat& sm = *dst[q];
+      sm.m = NH;
+      sm.K = NH;
+      sm.plan = plan;
+      proj_split_host(srcm[q], NH, NH, plan, sm.Kpad, sm.mtiles, planes, rexp);
+      uint16_t* dp = nullptr;
+      int* de = nullptr;
+      AL(c->allocs, &dp, planes.size());
+      AL(c->allocs, &de, rexp.size());
+      CK(cudaMemcpy(dp, planes.data(), sizeof(uint16_t) * planes.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(de, rexp.data(), sizeof(int) * rexp.size(), cudaMemcpyHostToDevice));
+      sm.planes = dp;
+      sm.rexp = de;
+    }
+    CK(proj_tc_prepare());
+    c->proj_tc = true;
+  }
   return PASM_OK;
 }
 
@@ -612,7 +670,8 @@ int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* 
       (o.score_norm != PASM_SCORE_A && o.score_norm != PASM_SCORE_B) ||
       (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED) ||
       (o.smoother != PASM_JACOBI && o.smoother != PASM_LEARNED) ||
-      (o.smoother == PASM_LEARNED && o.precision != PASM_MIXED))
+      (o.smoother == PASM_LEARNED && o.precision != PASM_MIXED) ||
+      (o.projection != PASM_PROJ_TENSOR && o.projection != PASM_PROJ_FP64))
     return PASM_EINVAL;
   int v = validate_levels(n_levels, A, M, P);
   if (v) return v;
@@ -737,8 +796,10 @@ int pasm_get(pasm_ctx* c, double* lambda, double* U, int* steps, int* status) {
   if (U) { int r = get_block(c, c->U, U, c->lv.back().n); if (r) return r; }
   if (steps) CK(cudaMemcpyAsync(steps, c->steps, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
   if (status) CK(cudaMemcpyAsync(status, c->status, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
+  int perr = 0;
+  CK(cudaMemcpyAsync(&perr, c->proj_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
-  return PASM_OK;
+  return perr ? PASM_ETIMEOUT : PASM_OK;
 }
 
 int pasm_solve(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0, double* lambda_out,
@@ -789,6 +850,32 @@ int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, d
   if (beta) CK(cudaMemcpyAsync(beta, c->bz, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
   if (zeta) CK(cudaMemcpyAsync(zeta, c->bz + c->ldk, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
   CK(cudaStreamSynchronize(c->s));
+  return PASM_OK;
+}
+
+int pasm_project(pasm_ctx* c, const double* b, const double* cc, double* bq, double* cq) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  if (!b || !cc || !bq || !cq) return PASM_EINVAL;
+  Scope sc(c);
+  const int NH = c->NH;
+  int before = 0, after = 0;
+  CK(cudaMemcpyAsync(&before, c->proj_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  int r = put_block(c, b, c->g, NH);
+  if (!r) r = put_block(c, cc, c->uH, NH);
+  if (r) return r;
+  project_bc(c, launcher(c), c->g, c->uH, c->bq, c->cq);
+  CK(cudaGetLastError());
+  r = get_block(c, c->bq, bq, NH);
+  if (!r) r = get_block(c, c->cq, cq, NH);
+  if (r) return r;
+  CK(cudaMemcpyAsync(&after, c->proj_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
+  return after != before ? PASM_ETIMEOUT : PASM_OK;
+}
+
+int pasm_projection_kind(pasm_ctx* c, int* kind) {
+  if (!c || !kind) return PASM_EINVAL;
+  *kind = c->proj_tc ? PASM_PROJ_TENSOR : PASM_PROJ_FP64;
   return PASM_OK;
 }
 
@@ -1037,7 +1124,7 @@ int pasm_trace_launches(pasm_ctx* c, int max, int* cls, int* rows, float* ms, do
 const char* pasm_kernel_class_name(int cls) {
   static const char* names[KC_N] = {"jacobi", "jacobi0", "resid", "spmm", "prolong", "dense", "outer_rhs",
                                     "outer_res", "axpy", "border", "colsum", "init", "secular", "update",
-                                    "count", "cast", "nn"};
+                                    "count", "cast", "nn", "proj"};
   return (cls >= 0 && cls < KC_N) ? names[cls] : "unknown";
 }
 

@@ -526,7 +526,7 @@ static size_t secular_smem(int NH) {
 }
 
 cudaError_t secular_prepare(int NH) {
-  return cudaFuncSetAttribute(k_secular, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)secular_smem(NH));
+  return allow_dynamic_smem((const void*)k_secular, secular_smem(NH));
 }
 
 void secular_select(const Launch& L, const SecularArgs& a) {

@@ -39,8 +39,9 @@ def write(name):
 
 
 HISTORIES = {
-    # name: (dim, N_fine, N_coarse, k, tol, max_steps)
-    "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40),
+    # name: (dim, N_fine, N_coarse, k, tol, max_steps, nested start)
+    "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40, False),
+    "square_h1024_H16_k64_nested_history": (2, 1024, 16, 64, 1e-10, 40, True),
 }
 
 
@@ -50,12 +51,12 @@ def write_history(name):
     pair; pairs freeze once their relative change is below tol."""
     import json
     import oracle
-    dim, N, Nc, k, tol, max_steps = HISTORIES[name]
+    dim, N, Nc, k, tol, max_steps, nested = HISTORIES[name]
     t = time.time()
     H = mg.build_hierarchy(dim, N, Nc)
     prob = oracle.Problem.from_hierarchy(H)
-    lam, U, steps, hist = oracle.solve(prob, k, tol=tol, max_steps=max_steps, history=True)
-    out = {"dim": dim, "N_fine": N, "N_coarse": Nc, "k": k, "tol": tol, "max_steps": max_steps,
+    lam, U, steps, hist = oracle.solve(prob, k, tol=tol, max_steps=max_steps, history=True, nested=nested)
+    out = {"dim": dim, "N_fine": N, "N_coarse": Nc, "k": k, "tol": tol, "max_steps": max_steps, "nested": nested,
            "steps": [int(s) for s in steps], "history": [[float(v) for v in row] for row in hist],
            "seconds": time.time() - t}
     with open(os.path.join(HERE, name + ".json"), "w") as f:
