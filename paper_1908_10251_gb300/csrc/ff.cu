@@ -1,0 +1,434 @@
+// Float64-accuracy kernels of the mixed-precision path in double-float
+// arithmetic (ff.cuh): the outer residuals of the defect correction
+// (Algorithm 1 step 1), the bordering products (the bordered matrix form of
+// Section 3.1), the transfer chains and the update.  Vectors that are gathered
+// through a sparse matrix are kept as (hi, lo) float pairs ("ff", 8 bytes per
+// entry like float64): the multigrid iterate u~, its products A u~ and M u~,
+// the intermediate levels of the transfer chains, and a per-step split copy of
+// U.  Matrix values are split once at setup.  The state U, the coarse vectors
+// and the eigenvalues stay float64.  Results carry about 2^-46 relative to the
+// sum of the magnitudes of their terms (float64: 2^-53), far below what the
+// float32 V-cycles of the mixed path resolve.
+#include "common.cuh"
+#include "ff.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace pasm {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Geo {
+  int tpr, ch;
+};
+// Row groups as in the float64 kernels: 16-byte chunks of 2 columns.
+Geo geometry_ff(int ldk) {
+  const int chunks = ldk / 2;
+  Geo g;
+  if (chunks <= 32) { g.tpr = chunks; g.ch = 1; }
+  else { g.tpr = 32; g.ch = chunks / 32; }
+  return g;
+}
+
+#define PASM_FF_DISPATCH(ch, ...)                          \
+  switch (ch) {                                            \
+    case 1: { constexpr int CH = 1; __VA_ARGS__; } break;  \
+    case 2: { constexpr int CH = 2; __VA_ARGS__; } break;  \
+    case 4: { constexpr int CH = 4; __VA_ARGS__; } break;  \
+    default: break;                                        \
+  }
+
+// Two consecutive entries (columns col, col + 1) of row i of a block vector,
+// as (hi, lo) pairs: from float pairs directly, from float64 by splitting.
+template <bool FF>
+__device__ __forceinline__ void load_pair(const double* __restrict__ X, size_t off, float (&h)[2], float (&l)[2]) {
+  if (FF) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(X + off));
+    h[0] = t.x; l[0] = t.y; h[1] = t.z; l[1] = t.w;
+  } else {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(X + off));
+    ff_split(t.x, h[0], l[0]);
+    ff_split(t.y, h[1], l[1]);
+  }
+}
+
+// acc += a_p X[ci_p, cols] for the N entries p .. p+N-1: index and value loads,
+// then the N row gathers, then the double-float products.
+template <int CH, int N, bool FFIN>
+__device__ __forceinline__ void gather_group_ff(const int* __restrict__ ci, const float2* __restrict__ av,
+                                                const double* __restrict__ X, int p, int lane, int tpr, int ldk,
+                                                float (&hi)[CH][2], float (&lo)[CH][2]) {
+  int j[N];
+  float2 a[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    j[u] = __ldg(ci + p + u);
+    a[u] = __ldg(av + p + u);
+  }
+  float xh[N][CH][2], xl[N][CH][2];
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) load_pair<FFIN>(X, (size_t)j[u] * ldk + (c * tpr + lane) * 2, xh[u][c], xl[u][c]);
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) ff_mac(hi[c][v], lo[c][v], a[u].x, a[u].y, xh[u][c][v], xl[u][c][v]);
+}
+
+// One row of S X in double-float (groups of 4 entries, then an exact remainder group).
+template <int CH, bool FFIN>
+__device__ __forceinline__ void gather_row_ff(const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const float2* __restrict__ av, const double* __restrict__ X, int row,
+                                              int lane, int tpr, int ldk, float (&hi)[CH][2], float (&lo)[CH][2]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c) hi[c][0] = hi[c][1] = lo[c][0] = lo[c][1] = 0.f;
+  int p = __ldg(rp + row);
+  const int p1 = __ldg(rp + row + 1);
+  for (; p + 4 <= p1; p += 4) gather_group_ff<CH, 4, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  const int rem = p1 - p;
+  if (rem == 3) gather_group_ff<CH, 3, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  else if (rem == 2) gather_group_ff<CH, 2, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  else if (rem == 1) gather_group_ff<CH, 1, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    ff_norm(hi[c][0], lo[c][0]);
+    ff_norm(hi[c][1], lo[c][1]);
+  }
+}
+
+// Store two entries as float pairs or, rounded, as float64.
+template <bool FF>
+__device__ __forceinline__ void store_pair(double* __restrict__ out, size_t off, const float (&h)[2],
+                                           const float (&l)[2]) {
+  if (FF) *reinterpret_cast<float4*>(out + off) = make_float4(h[0], l[0], h[1], l[1]);
+  else *reinterpret_cast<double2*>(out + off) = make_double2(ff_to_double(h[0], l[0]), ff_to_double(h[1], l[1]));
+}
+
+// Fd = lam .* (M U) stored as (hi, lo) float pairs, R = Fd - A U as float32
+// (U given as float pairs).
+template <int CH>
+__global__ void __launch_bounds__(kBlock)
+    k_outer_rhs_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
+                       const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
+                       const double* __restrict__ lam, const double* __restrict__ U, float2* __restrict__ Fd,
+                       float* __restrict__ R, int ldk, int tpr) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  float muh[CH][2], mul[CH][2], auh[CH][2], aul[CH][2];
+  gather_row_ff<CH, true>(mrp, mci, mval, U, row, lane, tpr, ldk, muh, mul);
+  gather_row_ff<CH, true>(arp, aci, aval, U, row, lane, tpr, ldk, auh, aul);
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    float f[2][2], r[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      float lh, ll;
+      ff_split(__ldg(lam + col + v), lh, ll);
+      ff_mul(lh, ll, muh[c][v], mul[c][v], f[v][0], f[v][1]);
+      r[v] = __fadd_rn(__fsub_rn(f[v][0], auh[c][v]), __fsub_rn(f[v][1], aul[c][v]));
+    }
+    *reinterpret_cast<float4*>(Fd + base + col) = make_float4(f[0][0], f[0][1], f[1][0], f[1][1]);
+    *reinterpret_cast<float2*>(R + base + col) = make_float2(r[0], r[1]);
+  }
+}
+
+// R = Fd - A X as float32 (Fd and X as float pairs).
+template <int CH>
+__global__ void __launch_bounds__(kBlock)
+    k_outer_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
+                   const float2* __restrict__ Fd, const double* __restrict__ X, float* __restrict__ R, int ldk,
+                   int tpr) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  float axh[CH][2], axl[CH][2];
+  gather_row_ff<CH, true>(arp, aci, aval, X, row, lane, tpr, ldk, axh, axl);
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    const float4 f = __ldg(reinterpret_cast<const float4*>(Fd + base + col));
+    const float r0 = __fadd_rn(__fsub_rn(f.x, axh[c][0]), __fsub_rn(f.y, axl[c][0]));
+    const float r1 = __fadd_rn(__fsub_rn(f.z, axh[c][1]), __fsub_rn(f.w, axl[c][1]));
+    *reinterpret_cast<float2*>(R + base + col) = make_float2(r0, r1);
+  }
+}
+
+// YA = A X, YM = M X (X, YA, YM as float pairs) and per-block partial sums of
+// X .* YA, X .* YM (double-float per thread, float64 across the block).
+template <int CH>
+__global__ void __launch_bounds__(kBlock)
+    k_border_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
+                const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
+                const double* __restrict__ X, double* __restrict__ YA, double* __restrict__ YM,
+                double* __restrict__ partials, int ldk, int tpr) {
+  extern __shared__ double red[];  // [rpb][2][ldk]
+  const int rpb = kBlock / tpr;
+  const int grp = threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  float sAh[CH][2], sAl[CH][2], sMh[CH][2], sMl[CH][2];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) sAh[c][v] = sAl[c][v] = sMh[c][v] = sMl[c][v] = 0.f;
+  for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
+    float yah[CH][2], yal[CH][2], ymh[CH][2], yml[CH][2];
+    gather_row_ff<CH, true>(arp, aci, aval, X, row, lane, tpr, ldk, yah, yal);
+    gather_row_ff<CH, true>(mrp, mci, mval, X, row, lane, tpr, ldk, ymh, yml);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const size_t off = base + (c * tpr + lane) * 2;
+      float xh[2], xl[2];
+      load_pair<true>(X, off, xh, xl);
+      store_pair<true>(YA, off, yah[c], yal[c]);
+      store_pair<true>(YM, off, ymh[c], yml[c]);
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        ff_mac(sAh[c][v], sAl[c][v], xh[v], xl[v], yah[c][v], yal[c][v]);
+        ff_mac(sMh[c][v], sMl[c][v], xh[v], xl[v], ymh[c][v], yml[c][v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      red[(grp * 2 + 0) * ldk + col + v] = ff_to_double(sAh[c][v], sAl[c][v]);
+      red[(grp * 2 + 1) * ldk + col + v] = ff_to_double(sMh[c][v], sMl[c][v]);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * ldk; t += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rpb; ++r) s += red[r * 2 * ldk + t];
+    partials[(size_t)blockIdx.x * 2 * ldk + t] = s;
+  }
+}
+
+// out = S X; FFIN / FFOUT: X / out as float pairs (else float64).
+template <int CH, bool FFIN, bool FFOUT>
+__global__ void __launch_bounds__(kBlock) k_spmm_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                     const float2* __restrict__ av, const double* __restrict__ X,
+                                                     double* __restrict__ out, int ldk, int tpr) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  float yh[CH][2], yl[CH][2];
+  gather_row_ff<CH, FFIN>(rp, ci, av, X, row, lane, tpr, ldk, yh, yl);
+  const size_t base = (size_t)row * ldk;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) store_pair<FFOUT>(out, base + (c * tpr + lane) * 2, yh[c], yl[c]);
+}
+
+// X = B + E with E float32, X as float pairs; B as float pairs (may alias X)
+// or float64.
+template <bool BFF>
+__global__ void k_axpy_ff(int64_t total, const double* B, const float* __restrict__ E, double* X) {
+  const int64_t np = total / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    float bh[2], bl[2];
+    load_pair<BFF>(B, 2 * i, bh, bl);
+    const float2 e = __ldg(reinterpret_cast<const float2*>(E + 2 * i));
+    const float ev[2] = {e.x, e.y};
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      float h = bh[v], l = bl[v];
+      ff_mac(h, l, ev[v], 0.f, 1.f, 0.f);
+      ff_norm(h, l);
+      bh[v] = h;
+      bl[v] = l;
+    }
+    store_pair<true>(X, 2 * i, bh, bl);
+  }
+}
+
+// Elementwise format conversions of block vectors.
+// in may equal out: each thread reads its two entries before writing them.
+__global__ void k_to_ff(int64_t total, const double* in, double* out) {
+  const int64_t np = total / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    float h[2], l[2];
+    load_pair<false>(in, 2 * i, h, l);
+    store_pair<true>(out, 2 * i, h, l);
+  }
+}
+__global__ void k_from_ff(int64_t total, const double* __restrict__ in, double* __restrict__ out) {
+  const int64_t np = total / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    float h[2], l[2];
+    load_pair<true>(in, 2 * i, h, l);
+    store_pair<false>(out, 2 * i, h, l);
+  }
+}
+
+// U[row][c] = upd[c] ? alpha[c] X[row][c] + (P W)[row][c] : U[row][c], X as
+// float pairs, W as float pairs (WFF) or float64; identity: P W = W.
+template <int CH, bool WFF>
+__global__ void __launch_bounds__(kBlock)
+    k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
+                const double* __restrict__ W, const double* __restrict__ X, const double* __restrict__ alpha,
+                const int* __restrict__ upd, double* __restrict__ U, int ldk, int tpr, int identity) {
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  float wh[CH][2], wl[CH][2];
+  const size_t base = (size_t)row * ldk;
+  if (identity) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) load_pair<WFF>(W, base + (c * tpr + lane) * 2, wh[c], wl[c]);
+  } else {
+    gather_row_ff<CH, WFF>(rp, ci, pv, W, row, lane, tpr, ldk, wh, wl);
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int col = (c * tpr + lane) * 2;
+    const size_t off = base + col;
+    float xh[2], xl[2];
+    load_pair<true>(X, off, xh, xl);
+    double2 u = *reinterpret_cast<const double2*>(U + off);
+    double r[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      float ah, al;
+      ff_split(__ldg(alpha + col + v), ah, al);
+      float h = wh[c][v], l = wl[c][v];
+      ff_mac(h, l, ah, al, xh[v], xl[v]);
+      r[v] = ff_to_double(h, l);
+    }
+    if (upd[col]) u.x = r[0];
+    if (upd[col + 1]) u.y = r[1];
+    *reinterpret_cast<double2*>(U + off) = u;
+  }
+}
+
+}  // namespace
+
+void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
+                           double* Fd, float* R, int ldk) {
+  const Geo g = geometry_ff(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.rows(A.n_rows);
+    L.begin(KC_OUTER_RHS, nnz * 12.0 + 2 * (n + 1) * 4.0 + n * ldk * (16.0 + 4.0), 2.0 * nnz * ldk + 2.0 * n * ldk);
+  }
+  PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH><<<grid, kBlock, 0, L.s>>>(
+                             A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, lam, U,
+                             reinterpret_cast<float2*>(Fd), R, ldk, g.tpr));
+  L.bump();
+}
+
+void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const double* X, float* R, int ldk) {
+  const Geo g = geometry_ff(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double n = A.n_rows, nnz = (double)A.nnz;
+    L.rows(A.n_rows);
+    L.begin(KC_OUTER_RES, nnz * 12.0 + (n + 1) * 4.0 + n * ldk * (16.0 + 4.0), 2.0 * nnz * ldk + n * ldk);
+  }
+  PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH><<<grid, kBlock, 0, L.s>>>(
+                             A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+  L.bump();
+}
+
+int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
+                       double* partials, int ldk, int max_blocks) {
+  const Geo g = geometry_ff(ldk);
+  const int rpb = kBlock / g.tpr;
+  int grid = std::min((A.n_rows + rpb - 1) / rpb, max_blocks);
+  if (grid < 1) grid = 1;
+  const size_t smem = (size_t)rpb * 2 * ldk * sizeof(double);
+  {
+    const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
+    L.rows(A.n_rows);
+    L.begin(KC_BORDER, nnz * 12.0 + 2 * (n + 1) * 4.0 + 3.0 * n * ldk * 8.0, 2.0 * nnz * ldk + 4.0 * n * ldk);
+  }
+  PASM_FF_DISPATCH(g.ch, k_border_ff<CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci,
+                                                                       M.vff, X, YA, YM, partials, ldk, g.tpr));
+  L.bump();
+  return grid;
+}
+
+void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk) {
+  if (S.n_rows == 0) return;
+  const Geo g = geometry_ff(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (S.n_rows + rpb - 1) / rpb;
+  {
+    const double rows = S.n_rows, cols = S.n_cols, nnz = (double)S.nnz;
+    L.rows(S.n_rows);
+    L.begin(KC_SPMM, nnz * 12.0 + (rows + 1) * 4.0 + cols * ldk * 8.0 + rows * ldk * 8.0, 2.0 * nnz * ldk);
+  }
+#define PASM_FF_SPMM(FI, FO) \
+  PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, X, out, ldk, g.tpr))
+  if (x_ff && out_ff) { PASM_FF_SPMM(true, true); }
+  else if (x_ff) { PASM_FF_SPMM(true, false); }
+  else if (out_ff) { PASM_FF_SPMM(false, true); }
+  else { PASM_FF_SPMM(false, false); }
+#undef PASM_FF_SPMM
+  L.bump();
+}
+
+static int stream_grid(int64_t total) { return (int)std::min<int64_t>((total / 2 + kBlock - 1) / kBlock, 152 * 16); }
+
+void axpy_ff(const Launch& L, int n, const double* B, bool b_ff, const float* E, double* X, int ldk) {
+  const int64_t total = (int64_t)n * ldk;
+  L.begin(KC_AXPY, (double)total * (16.0 + 4.0), (double)total);
+  if (b_ff) k_axpy_ff<true><<<stream_grid(total), kBlock, 0, L.s>>>(total, B, E, X);
+  else k_axpy_ff<false><<<stream_grid(total), kBlock, 0, L.s>>>(total, B, E, X);
+  L.bump();
+}
+
+void to_ff(const Launch& L, int64_t total, const double* in, double* out) {
+  L.begin(KC_CAST, (double)total * 16.0, 0.0);
+  k_to_ff<<<stream_grid(total), kBlock, 0, L.s>>>(total, in, out);
+  L.bump();
+}
+
+void from_ff(const Launch& L, int64_t total, const double* in, double* out) {
+  L.begin(KC_CAST, (double)total * 16.0, (double)total);
+  k_from_ff<<<stream_grid(total), kBlock, 0, L.s>>>(total, in, out);
+  L.bump();
+}
+
+void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
+                     const double* alpha, const int* upd, double* U, int ldk) {
+  const Geo g = geometry_ff(ldk);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (n + rpb - 1) / rpb;
+  const int identity = P ? 0 : 1;
+  {
+    const double nn = n, nnz = P ? (double)P->nnz : 0.0, cols = P ? (double)P->n_cols : nn;
+    L.begin(KC_UPDATE, nnz * 12.0 + (nn + 1) * 4.0 + cols * ldk * 8.0 + 3.0 * nn * ldk * 8.0,
+            2.0 * nnz * ldk + 2.0 * nn * ldk);
+  }
+  const int* rp = P ? P->rp : nullptr;
+  const int* ci = P ? P->ci : nullptr;
+  const float2* pv = P ? P->vff : nullptr;
+  if (w_ff) {
+    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, true><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, ldk,
+                                                                            g.tpr, identity));
+  } else {
+    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, false><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, ldk,
+                                                                             g.tpr, identity));
+  }
+  L.bump();
+}
+
+}  // namespace pasm

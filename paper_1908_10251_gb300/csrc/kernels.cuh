@@ -15,6 +15,7 @@ struct DCsr {
   int* ci = nullptr;
   double* v64 = nullptr;
   float* v32 = nullptr;
+  float2* vff = nullptr;  // (hi, lo) float split of v64 for the double-float kernels (mixed precision)
 };
 
 template <typename T> inline const T* vals(const DCsr& m);
@@ -128,6 +129,30 @@ void update_pairs(const Launch& L, const DCsr& P, const double* W, const double*
 // Same with P = identity (single-level hierarchy): U = alpha X + W.
 void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
                            const int* upd, double* U, int ldk);
+
+// ----------------------------------------------------------------------------------------------
+// Double-float versions of the float64-accuracy kernels (ff.cu), used in mixed
+// precision.  A block vector "in pairs" holds (hi, lo) floats in place of each
+// float64 (same size and layout); matrices go through S.vff.
+// Fd = lam .* (M U) (pairs), R = Fd - A U (float32); U in pairs.
+void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
+                           double* Fd, float* R, int ldk);
+// R = Fd - A X (float32); Fd and X in pairs.
+void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const double* X, float* R, int ldk);
+// YA = A X, YM = M X (X, YA, YM in pairs) and float64 partial sums as border_products.
+int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
+                       double* partials, int ldk, int max_blocks);
+// out = S X; x_ff / out_ff: X / out in pairs (else float64).
+void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk);
+// X = B + E (X in pairs; B in pairs if b_ff, else float64; X may alias B).
+void axpy_ff(const Launch& L, int n, const double* B, bool b_ff, const float* E, double* X, int ldk);
+// Conversions of total entries: float64 -> pairs (may be in place), pairs -> float64.
+void to_ff(const Launch& L, int64_t total, const double* in, double* out);
+void from_ff(const Launch& L, int64_t total, const double* in, double* out);
+// U = alpha X + P W for updated pairs (float64 U, X in pairs, W in pairs if
+// w_ff); P == nullptr means P = identity on n rows.
+void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
+                     const double* alpha, const int* upd, double* U, int ldk);
 
 // ----------------------------------------------------------------------------------------------
 // Float64-accurate dense product C = A B on the tensor cores (proj_tc.cu).

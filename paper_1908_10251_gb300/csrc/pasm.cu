@@ -86,6 +86,7 @@ struct pasm_ctx {
   int k = 0, ldk = 0;
   double tol = 0.0;
   double *U = nullptr, *Fd = nullptr, *X = nullptr, *YA = nullptr, *YM = nullptr;
+  double* Uff = nullptr;  // mixed precision: U split into (hi, lo) float pairs for the gathers
   double *lam = nullptr, *lam2 = nullptr, *alpha = nullptr, *bz = nullptr, *bq = nullptr, *cq = nullptr,
          *g = nullptr, *uH = nullptr, *partials = nullptr;
   int *active = nullptr, *upd = nullptr, *steps = nullptr, *status = nullptr, *nact = nullptr, *diag = nullptr;
@@ -160,7 +161,7 @@ int check_csr(const pasm_csr& m, int rows, int cols) {
   return PASM_OK;
 }
 
-int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32) {
+int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32, bool split_ff) {
   d.n_rows = h.n_rows; d.n_cols = h.n_cols; d.nnz = h.nnz;
   AL(c->allocs, &d.rp, (size_t)h.n_rows + 1);
   AL(c->allocs, &d.ci, (size_t)h.nnz);
@@ -174,6 +175,16 @@ int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32) {
     AL(c->allocs, &d.v32, (size_t)h.nnz);
     std::vector<float> f(h.val, h.val + h.nnz);
     if (h.nnz) CK(cudaMemcpy(d.v32, f.data(), sizeof(float) * (size_t)h.nnz, cudaMemcpyHostToDevice));
+  }
+  if (split_ff) {
+    // hi = nearest float, lo = nearest float of the remainder (about 48 bits)
+    AL(c->allocs, &d.vff, (size_t)h.nnz);
+    std::vector<float2> f((size_t)h.nnz);
+    for (int64_t q = 0; q < h.nnz; ++q) {
+      const float hi = (float)h.val[q];
+      f[(size_t)q] = make_float2(hi, (float)(h.val[q] - (double)hi));
+    }
+    if (h.nnz) CK(cudaMemcpy(d.vff, f.data(), sizeof(float2) * (size_t)h.nnz, cudaMemcpyHostToDevice));
   }
   return PASM_OK;
 }
@@ -316,6 +327,19 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
   const Launch L = launcher(c);
   LevelDev& v = c->lv[lt];
   T* Ftop = (T*)v.vF;
+  if (Fused<T>::on) {
+    // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
+    to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
+    outer_rhs_residual_ff(L, v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
+    T* e = vcycle<T>(c, lt);
+    axpy_ff(L, v.n, U, false, (const float*)e, X, c->ldk);
+    for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
+      outer_residual_ff(L, v.A, c->Fd, X, (float*)Ftop, c->ldk);
+      e = vcycle<T>(c, lt);
+      axpy_ff(L, v.n, X, true, (const float*)e, X, c->ldk);
+    }
+    return;
+  }
   outer_rhs_residual<T>(L, v.A, v.M, lam, U, c->Fd, Ftop, c->ldk);
   T* e = vcycle<T>(c, lt);
   outer_axpy<T>(L, v.n, U, e, X, c->ldk);
@@ -357,13 +381,21 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   const Launch L = launcher(c);
   LevelDev& v = c->lv[lt];
   const int ldk = c->ldk;
-  const int nb = border_products(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
+  const bool ff = c->opts.precision == PASM_MIXED;
+  const int nb = ff ? border_products_ff(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks)
+                    : border_products(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
   column_sums(L, c->partials, nb, 2, ldk, c->bz);
   const double* sa = c->YA;
   const double* sm = c->YM;
   for (int l = lt; l >= 1; --l) {
-    rowop<double>(L, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
-    rowop<double>(L, OP_SPMM, c->lv[l].R, sm, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BM, ldk);
+    if (ff) {
+      // pairs down to level 1, float64 on the coarse level for the projection
+      spmm_ff(L, c->lv[l].R, sa, true, c->lv[l - 1].BA, l - 1 >= 1, ldk);
+      spmm_ff(L, c->lv[l].R, sm, true, c->lv[l - 1].BM, l - 1 >= 1, ldk);
+    } else {
+      rowop<double>(L, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
+      rowop<double>(L, OP_SPMM, c->lv[l].R, sm, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BM, ldk);
+    }
     sa = c->lv[l - 1].BA;
     sm = c->lv[l - 1].BM;
   }
@@ -381,11 +413,15 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   else
     dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, false, c->g, c->uH, ldk);
   const double* w = c->uH;
+  bool w_ff = false;
   for (int l = 1; l < lt; ++l) {
-    rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
+    if (ff) spmm_ff(L, c->lv[l].P, w, w_ff, c->lv[l].BA, true, ldk);
+    else rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
     w = c->lv[l].BA;
+    w_ff = ff;
   }
-  if (lt >= 1) update_pairs(L, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
+  if (ff) update_pairs_ff(L, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, ldk);
+  else if (lt >= 1) update_pairs(L, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
   else update_pairs_identity(L, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
 }
 
@@ -418,6 +454,7 @@ int alloc_k(pasm_ctx* c, int k) {
   auto& K = c->kallocs;
   AL(K, &c->U, n * ldk); AL(K, &c->Fd, n * ldk); AL(K, &c->X, n * ldk);
   AL(K, &c->YA, n * ldk); AL(K, &c->YM, n * ldk);
+  if (c->opts.precision == PASM_MIXED) AL(K, &c->Uff, n * ldk);
   for (int l = 0; l < c->nlev; ++l) {
     LevelDev& v = c->lv[l];
     const size_t m = (size_t)v.n * ldk;
@@ -560,8 +597,8 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
   for (int l = 0; l < n_levels; ++l) c->lv[(size_t)l].n = A[l].n_rows;
   for (int l = 0; l < n_levels; ++l) {
     LevelDev& v = c->lv[(size_t)l];
-    int r = upload_csr(c, A[l], v.A, mixed);
-    if (!r) r = upload_csr(c, M[l], v.M, false);
+    int r = upload_csr(c, A[l], v.A, mixed, mixed);
+    if (!r) r = upload_csr(c, M[l], v.M, false, mixed);
     if (r) return r;
     std::vector<double> d((size_t)v.n, 0.0);
     for (int i = 0; i < v.n; ++i)
@@ -582,13 +619,13 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
     }
     if (l >= 1) {
       const pasm_csr& p = P[l - 1];
-      r = upload_csr(c, p, v.P, mixed);
+      r = upload_csr(c, p, v.P, mixed, mixed);
       if (r) return r;
       std::vector<int32_t> rp, ci;
       std::vector<double> rv;
       transpose_csr(p, rp, ci, rv);
       pasm_csr rt{p.n_cols, p.n_rows, p.nnz, rp.data(), ci.data(), rv.data()};
-      r = upload_csr(c, rt, v.R, mixed);
+      r = upload_csr(c, rt, v.R, mixed, mixed);
       if (r) return r;
     }
   }
@@ -826,7 +863,12 @@ int pasm_bvp(pasm_ctx* c, const double* lambda, const double* U, double* Uhat) {
   if (r) return r;
   bvp(c, c->nlev - 1, c->lam2, c->YM, c->X);
   CK(cudaGetLastError());
-  r = get_block(c, c->X, Uhat, nf);
+  const double* xout = c->X;
+  if (c->opts.precision == PASM_MIXED) {  // u~ comes back in (hi, lo) pairs
+    from_ff(launcher(c), (int64_t)nf * c->ldk, c->X, c->YA);
+    xout = c->YA;
+  }
+  r = get_block(c, xout, Uhat, nf);
   if (r) return r;
   CK(cudaStreamSynchronize(c->s));
   return PASM_OK;
@@ -842,6 +884,7 @@ int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, d
   if (!r) r = set_active(c, c->active2, c->steps2, c->status2);
   if (r) return r;
   CK(cudaMemcpyAsync(c->Fd, c->X, sizeof(double) * (size_t)nf * c->ldk, cudaMemcpyDeviceToDevice, c->s));
+  if (c->opts.precision == PASM_MIXED) to_ff(launcher(c), (int64_t)nf * c->ldk, c->X, c->X);
   PairState ps{c->lam2, c->active2, c->steps2, c->status2, c->Fd, 0.0};
   augmented(c, c->nlev - 1, c->X, ps);
   CK(cudaGetLastError());
