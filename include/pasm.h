@@ -65,6 +65,23 @@ enum { PASM_INIT_COARSE = 0, PASM_INIT_NESTED = 1 };
 enum { PASM_JACOBI = 0, PASM_LEARNED = 1 };       /* post-smoother               */
 enum { PASM_PROJ_TENSOR = 0, PASM_PROJ_FP64 = 1 };  /* coarse projection product */
 
+/* Kernel kinds whose tile shape the autotuner chooses (see pasm_tiles). */
+enum {
+  PASM_TILE_JACOBI = 0,         /* damped Jacobi sweep                               */
+  PASM_TILE_JACOBI2_ZERO,       /* two sweeps from a zero guess (float32 cycles)     */
+  PASM_TILE_RESID_RESTRICT,     /* residual + restriction (float32 cycles)           */
+  PASM_TILE_RESID,              /* residual (float64 cycles)                         */
+  PASM_TILE_RESTRICT,           /* restriction (float64 cycles)                      */
+  PASM_TILE_PROLONG,            /* prolongate and correct                            */
+  PASM_TILE_OUTER_RHS,          /* f = lambda M u and the first outer residual       */
+  PASM_TILE_OUTER_RES,          /* later outer residuals                             */
+  PASM_TILE_BORDER,             /* A u~, M u~ and their dot products                 */
+  PASM_TILE_CHAIN_R,            /* restriction chain of A u~, M u~                   */
+  PASM_TILE_CHAIN_P,            /* prolongation chain of u_H                         */
+  PASM_TILE_UPDATE,             /* u = alpha u~ + P_c u_H                            */
+  PASM_TILE_N
+};
+
 /* A sparse matrix in CSR form: n_rows x n_cols, nnz entries, 32-bit indices,
  * float64 values, column indices ascending within each row. */
 typedef struct {
@@ -104,6 +121,11 @@ typedef struct {
                           to float64 (error about 2^-56 N_H max|Q| max|b|);
                           PASM_PROJ_FP64: float64 CUDA-core products
                           [PASM_PROJ_TENSOR]                                    */
+  int autotune;        /* 1: at the first pasm_init for a block width, time each
+                          row-group tile shape (16-byte chunks per thread: 1, 2,
+                          4, 8) of every sparse kernel on every level with at
+                          least 16384 rows and keep the fastest; 0: fixed
+                          default shapes [1]                                     */
 } pasm_opts;
 
 typedef struct pasm_ctx pasm_ctx;
@@ -175,6 +197,12 @@ int pasm_augmented(pasm_ctx* ctx, const double* lambda_prev, const double* Uhat,
  * step.  Errors: PASM_ESTATE, PASM_EINVAL (NULL pointer), PASM_ETIMEOUT (a
  * tensor-core wait gave up; outputs then incomplete). */
 int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, double* cq);
+
+/* The tile shapes in use on `level`: chunks_per_thread[PASM_TILE_N] receives,
+ * per kernel kind, the 16-byte chunks of a block-vector row each thread
+ * handles (0 = the default shape: one chunk, or as many as keep at most 32
+ * threads per row).  Errors: PASM_EINVAL. */
+int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 
 /* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else
  * PASM_PROJ_FP64. */

@@ -27,6 +27,9 @@ PASM_SCORE_A, PASM_SCORE_B = 0, 1
 PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
 PASM_JACOBI, PASM_LEARNED = 0, 1
 PASM_PROJ_TENSOR, PASM_PROJ_FP64 = 0, 1
+TILE_KINDS = ("jacobi", "jacobi2_zero", "resid_restrict", "resid", "restrict", "prolong", "outer_rhs",
+              "outer_res", "border", "chain_r", "chain_p", "update")
+PASM_TILE_N = len(TILE_KINDS)
 NN_WEIGHTS = 2592
 
 
@@ -39,7 +42,7 @@ class pasm_opts(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("cycles_per_step", ctypes.c_int), ("max_steps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("projection", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("projection", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class PasmError(RuntimeError):
@@ -80,6 +83,7 @@ def load_library():
         "pasm_coarse_eigs": (I, [P, P, P]),
         "pasm_project": (I, [P, P, P, P, P]),
         "pasm_projection_kind": (I, [P, ctypes.POINTER(I)]),
+        "pasm_tiles": (I, [P, I, P]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
@@ -216,6 +220,13 @@ def pasm_augmented(ctx: Context, lam_prev, Uhat, lambda_out=None, U_out=None, be
 def pasm_project(ctx: Context, b, c, bq, cq):
     """bq = Q^T b, cq = Q^T c (N_H x k each, host or device)."""
     _check(load_library().pasm_project(ctx.handle, _ptr(b), _ptr(c), _ptr(bq), _ptr(cq)), "pasm_project")
+
+
+def pasm_tiles(ctx: Context, level: int):
+    """{kernel kind: 16-byte chunks per thread (0 = default)} on `level`."""
+    out = np.zeros(PASM_TILE_N, dtype=np.int32)
+    _check(load_library().pasm_tiles(ctx.handle, level, out.ctypes.data), "pasm_tiles")
+    return dict(zip(TILE_KINDS, (int(v) for v in out)))
 
 
 def pasm_projection_kind(ctx: Context) -> int:

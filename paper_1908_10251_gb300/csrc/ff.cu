@@ -23,12 +23,17 @@ constexpr int kBlock = 256;
 struct Geo {
   int tpr, ch;
 };
-// Row groups as in the float64 kernels: 16-byte chunks of 2 columns.
-Geo geometry_ff(int ldk) {
+// Row groups as in the float64 kernels: 16-byte chunks of 2 columns; pref as
+// in the float64 geometry (chunks per thread chosen by the autotuner).
+Geo geometry_ff(int ldk, int pref) {
   const int chunks = ldk / 2;
   Geo g;
   if (chunks <= 32) { g.tpr = chunks; g.ch = 1; }
   else { g.tpr = 32; g.ch = chunks / 32; }
+  if ((pref == 1 || pref == 2 || pref == 4 || pref == 8) && chunks % pref == 0 && chunks / pref <= 32) {
+    g.tpr = chunks / pref;
+    g.ch = pref;
+  }
   return g;
 }
 
@@ -37,6 +42,7 @@ Geo geometry_ff(int ldk) {
     case 1: { constexpr int CH = 1; __VA_ARGS__; } break;  \
     case 2: { constexpr int CH = 2; __VA_ARGS__; } break;  \
     case 4: { constexpr int CH = 4; __VA_ARGS__; } break;  \
+    case 8: { constexpr int CH = 8; __VA_ARGS__; } break;  \
     default: break;                                        \
   }
 
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kBlock)
 
 void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
                            double* Fd, float* R, int ldk) {
-  const Geo g = geometry_ff(ldk);
+  const Geo g = geometry_ff(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
@@ -334,7 +340,7 @@ void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const 
 }
 
 void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const double* X, float* R, int ldk) {
-  const Geo g = geometry_ff(ldk);
+  const Geo g = geometry_ff(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
@@ -349,7 +355,10 @@ void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const d
 
 int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
                        double* partials, int ldk, int max_blocks) {
-  const Geo g = geometry_ff(ldk);
+  Geo g = geometry_ff(ldk, L.geo);
+  // the per-block reduction buffer (rows per block x 2 x ldk doubles) stays within the
+  // default 48 KB of dynamic shared memory; a tile shape that needs more is not used
+  if ((size_t)(kBlock / g.tpr) * 2 * ldk * sizeof(double) > 48 * 1024) g = geometry_ff(ldk, 0);
   const int rpb = kBlock / g.tpr;
   int grid = std::min((A.n_rows + rpb - 1) / rpb, max_blocks);
   if (grid < 1) grid = 1;
@@ -367,7 +376,7 @@ int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const doub
 
 void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk) {
   if (S.n_rows == 0) return;
-  const Geo g = geometry_ff(ldk);
+  const Geo g = geometry_ff(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (S.n_rows + rpb - 1) / rpb;
   {
@@ -409,7 +418,7 @@ void from_ff(const Launch& L, int64_t total, const double* in, double* out) {
 
 void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
                      const double* alpha, const int* upd, double* U, int ldk) {
-  const Geo g = geometry_ff(ldk);
+  const Geo g = geometry_ff(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (n + rpb - 1) / rpb;
   const int identity = P ? 0 : 1;

@@ -19,13 +19,21 @@ static constexpr int kBlock = 256;
 struct Geo {
   int tpr, ch;
 };
+// Row-group geometry for ldk columns of T: chunks = ldk / (16 / sizeof(T))
+// 16-byte chunks per row, tpr threads per row, ch chunks per thread.  The
+// default is the fewest chunks per thread with tpr <= 32; pref (1, 2, 4, 8;
+// chosen by the autotuner) is taken when it divides the row with tpr <= 32.
 template <typename T>
-static Geo geometry(int ldk) {
+static Geo geometry(int ldk, int pref = 0) {
   const int V = Vec16<T>::N;
   int chunks = ldk / V;
   Geo g;
   if (chunks <= 32) { g.tpr = chunks; g.ch = 1; }
   else { g.tpr = 32; g.ch = chunks / 32; }
+  if ((pref == 1 || pref == 2 || pref == 4 || pref == 8) && chunks % pref == 0 && chunks / pref <= 32) {
+    g.tpr = chunks / pref;
+    g.ch = pref;
+  }
   return g;
 }
 
@@ -34,6 +42,7 @@ static Geo geometry(int ldk) {
     case 1: { constexpr int CH = 1; __VA_ARGS__; } break;  \
     case 2: { constexpr int CH = 2; __VA_ARGS__; } break;  \
     case 4: { constexpr int CH = 4; __VA_ARGS__; } break;  \
+    case 8: { constexpr int CH = 8; __VA_ARGS__; } break;  \
     default: break;                                        \
   }
 
@@ -134,7 +143,7 @@ template <typename T>
 void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, const T* Z, const T* dinv, T omega,
            T* out, int ldk) {
   if (S.n_rows == 0) return;
-  Geo g = geometry<T>(ldk);
+  Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (S.n_rows + rpb - 1) / rpb;
   const T* av = vals<T>(S);
@@ -275,7 +284,7 @@ __global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int* __
 template <typename T>
 void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const T* F, T* out, int ldk) {
   if (A.n_rows == 0) return;
-  Geo g = geometry<T>(ldk);
+  Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
@@ -292,7 +301,7 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
 template <typename T>
 void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, const T* F, T* out, int ldk) {
   if (R.n_rows == 0) return;
-  Geo g = geometry<T>(ldk);
+  Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (R.n_rows + rpb - 1) / rpb;
   {
@@ -393,12 +402,12 @@ __global__ void k_outer_axpy(int64_t total, const double* B, const TV* __restric
   }
 }
 
-static Geo geometry64(int ldk) { return geometry<double>(ldk); }
+static Geo geometry64(int ldk, int pref = 0) { return geometry<double>(ldk, pref); }
 
 template <typename TV>
 void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
                         double* Fd, TV* R, int ldk) {
-  Geo g = geometry64(ldk);
+  Geo g = geometry64(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
@@ -413,7 +422,7 @@ void outer_rhs_residual(const Launch& L, const DCsr& A, const DCsr& M, const dou
 }
 template <typename TV>
 void outer_residual(const Launch& L, const DCsr& A, const double* Fd, const double* X, TV* R, int ldk) {
-  Geo g = geometry64(ldk);
+  Geo g = geometry64(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (A.n_rows + rpb - 1) / rpb;
   {
@@ -494,7 +503,10 @@ __global__ void __launch_bounds__(kBlock) k_border(int n, const int* __restrict_
 
 int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
                     double* partials, int ldk, int max_blocks) {
-  Geo g = geometry64(ldk);
+  Geo g = geometry64(ldk, L.geo);
+  // the per-block reduction buffer (rows per block x 2 x ldk doubles) stays within the
+  // default 48 KB of dynamic shared memory; a tile shape that needs more is not used
+  if ((size_t)(kBlock / g.tpr) * 2 * ldk * sizeof(double) > 48 * 1024) g = geometry64(ldk, 0);
   const int rpb = kBlock / g.tpr;
   int grid = std::min((A.n_rows + rpb - 1) / rpb, max_blocks);
   if (grid < 1) grid = 1;
@@ -613,7 +625,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, const int* __restrict_
 
 void update_pairs(const Launch& L, const DCsr& P, const double* W, const double* X, const double* alpha,
                   const int* upd, double* U, int ldk) {
-  Geo g = geometry64(ldk);
+  Geo g = geometry64(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (P.n_rows + rpb - 1) / rpb;
   {
@@ -627,7 +639,7 @@ void update_pairs(const Launch& L, const DCsr& P, const double* W, const double*
 }
 void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
                            const int* upd, double* U, int ldk) {
-  Geo g = geometry64(ldk);
+  Geo g = geometry64(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (n + rpb - 1) / rpb;
   L.begin(KC_UPDATE, 4.0 * n * ldk * 8.0, 2.0 * n * ldk);

@@ -41,6 +41,7 @@ struct Launch {
   cudaStream_t s = nullptr;
   int* counter = nullptr;
   Tracer* tr = nullptr;
+  int geo = 0;  // row-group kernels: 16-byte chunks per thread (0 = default; set by the autotuner)
   void begin(int cls, double bytes, double flops) const { if (tr) tracer_begin(tr, s, cls, bytes, flops); }
   void rows(int n) const { if (tr) tracer_rows(tr, n); }
   void bump() const {

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <new>
 #include <string>
 #include <vector>
@@ -118,6 +119,9 @@ struct pasm_ctx {
   int* proj_err = nullptr;                 // timed-out tensor-core waits of the projection kernel
   unsigned long long* proj_hl = nullptr;   // integer sums of the projection (k-dependent scratch)
   unsigned int* proj_tickets = nullptr;
+  // autotuned row-group geometry per level and kernel kind (0 = default), for block width tuned_ldk
+  std::vector<std::array<int, PASM_TILE_N>> geo;
+  int tuned_ldk = 0;
   int launches = 0;
   int last_launches = 0;
   bool initialized = false;
@@ -232,6 +236,13 @@ Launch launcher(pasm_ctx* c) {
   return L;
 }
 
+// launcher with the autotuned geometry of kernel kind `kind` on level l
+Launch launcher(pasm_ctx* c, int l, int kind) {
+  Launch L = launcher(c);
+  if (l >= 0 && l < (int)c->geo.size()) L.geo = c->geo[(size_t)l][(size_t)kind];
+  return L;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Multigrid V-cycle for A_l E = F_l from a zero guess; returns the buffer holding E.
 template <typename T> const T* ainv(pasm_ctx* c);
@@ -290,7 +301,7 @@ T* vcycle(pasm_ctx* c, int l) {
   T* tmp = Tm;
   int s = 0;
   if (fuse && c->opts.nu_pre >= 2) {
-    jacobi2_zero<T>(L, v.A, dinv<T>(v), om, F, cur, ldk);
+    jacobi2_zero<T>(launcher(c, l, PASM_TILE_JACOBI2_ZERO), v.A, dinv<T>(v), om, F, cur, ldk);
     s = 2;
   } else if (c->opts.nu_pre >= 1) {
     jacobi_zero<T>(L, v.n, dinv<T>(v), om, F, cur, ldk);
@@ -299,22 +310,23 @@ T* vcycle(pasm_ctx* c, int l) {
     cudaMemsetAsync(cur, 0, sizeof(T) * (size_t)v.n * ldk, c->s);
   }
   for (; s < c->opts.nu_pre; ++s) {
-    rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
+    rowop<T>(launcher(c, l, PASM_TILE_JACOBI), OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
   if (fuse) {
-    resid_restrict<T>(L, v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
+    resid_restrict<T>(launcher(c, l, PASM_TILE_RESID_RESTRICT), v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
   } else {
-    rowop<T>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
-    rowop<T>(L, OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om, (T*)c->lv[l - 1].vF, ldk);
+    rowop<T>(launcher(c, l, PASM_TILE_RESID), OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
+    rowop<T>(launcher(c, l, PASM_TILE_RESTRICT), OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om,
+             (T*)c->lv[l - 1].vF, ldk);
   }
   T* ec = vcycle<T>(c, l - 1);
-  rowop<T>(L, OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
+  rowop<T>(launcher(c, l, PASM_TILE_PROLONG), OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
   s = 0;
   if (Fused<T>::on) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
   if (s == 1) std::swap(cur, tmp);
   for (; s < c->opts.nu_post; ++s) {
-    rowop<T>(L, OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
+    rowop<T>(launcher(c, l, PASM_TILE_JACOBI), OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
   return cur;
@@ -330,21 +342,21 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
   if (Fused<T>::on) {
     // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
     to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
-    outer_rhs_residual_ff(L, v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
+    outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
     T* e = vcycle<T>(c, lt);
     axpy_ff(L, v.n, U, false, (const float*)e, X, c->ldk);
     for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
-      outer_residual_ff(L, v.A, c->Fd, X, (float*)Ftop, c->ldk);
+      outer_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RES), v.A, c->Fd, X, (float*)Ftop, c->ldk);
       e = vcycle<T>(c, lt);
       axpy_ff(L, v.n, X, true, (const float*)e, X, c->ldk);
     }
     return;
   }
-  outer_rhs_residual<T>(L, v.A, v.M, lam, U, c->Fd, Ftop, c->ldk);
+  outer_rhs_residual<T>(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, U, c->Fd, Ftop, c->ldk);
   T* e = vcycle<T>(c, lt);
   outer_axpy<T>(L, v.n, U, e, X, c->ldk);
   for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
-    outer_residual<T>(L, v.A, c->Fd, X, Ftop, c->ldk);
+    outer_residual<T>(launcher(c, lt, PASM_TILE_OUTER_RES), v.A, c->Fd, X, Ftop, c->ldk);
     e = vcycle<T>(c, lt);
     outer_axpy<T>(L, v.n, X, e, X, c->ldk);
   }
@@ -382,19 +394,22 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   LevelDev& v = c->lv[lt];
   const int ldk = c->ldk;
   const bool ff = c->opts.precision == PASM_MIXED;
-  const int nb = ff ? border_products_ff(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks)
-                    : border_products(L, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
+  const Launch Lb = launcher(c, lt, PASM_TILE_BORDER);
+  const int nb = ff ? border_products_ff(Lb, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks)
+                    : border_products(Lb, v.A, v.M, X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
   column_sums(L, c->partials, nb, 2, ldk, c->bz);
   const double* sa = c->YA;
   const double* sm = c->YM;
   for (int l = lt; l >= 1; --l) {
     if (ff) {
       // pairs down to level 1, float64 on the coarse level for the projection
-      spmm_ff(L, c->lv[l].R, sa, true, c->lv[l - 1].BA, l - 1 >= 1, ldk);
-      spmm_ff(L, c->lv[l].R, sm, true, c->lv[l - 1].BM, l - 1 >= 1, ldk);
+      const Launch Lr = launcher(c, l, PASM_TILE_CHAIN_R);
+      spmm_ff(Lr, c->lv[l].R, sa, true, c->lv[l - 1].BA, l - 1 >= 1, ldk);
+      spmm_ff(Lr, c->lv[l].R, sm, true, c->lv[l - 1].BM, l - 1 >= 1, ldk);
     } else {
-      rowop<double>(L, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
-      rowop<double>(L, OP_SPMM, c->lv[l].R, sm, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BM, ldk);
+      const Launch Lr = launcher(c, l, PASM_TILE_CHAIN_R);
+      rowop<double>(Lr, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
+      rowop<double>(Lr, OP_SPMM, c->lv[l].R, sm, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BM, ldk);
     }
     sa = c->lv[l - 1].BA;
     sm = c->lv[l - 1].BM;
@@ -415,14 +430,16 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   const double* w = c->uH;
   bool w_ff = false;
   for (int l = 1; l < lt; ++l) {
-    if (ff) spmm_ff(L, c->lv[l].P, w, w_ff, c->lv[l].BA, true, ldk);
-    else rowop<double>(L, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
+    const Launch Lp = launcher(c, l, PASM_TILE_CHAIN_P);
+    if (ff) spmm_ff(Lp, c->lv[l].P, w, w_ff, c->lv[l].BA, true, ldk);
+    else rowop<double>(Lp, OP_SPMM, c->lv[l].P, w, nullptr, nullptr, nullptr, 0.0, c->lv[l].BA, ldk);
     w = c->lv[l].BA;
     w_ff = ff;
   }
-  if (ff) update_pairs_ff(L, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, ldk);
-  else if (lt >= 1) update_pairs(L, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
-  else update_pairs_identity(L, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
+  const Launch Lu = launcher(c, lt, PASM_TILE_UPDATE);
+  if (ff) update_pairs_ff(Lu, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, ldk);
+  else if (lt >= 1) update_pairs(Lu, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
+  else update_pairs_identity(Lu, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
 }
 
 // One correction step for all active pairs on the finest level.
@@ -537,6 +554,7 @@ void pasm_default_opts(pasm_opts* o) {
   o->use_graph = 1;
   o->smoother = PASM_JACOBI;
   o->projection = PASM_PROJ_TENSOR;
+  o->autotune = 1;
 }
 
 const char* pasm_strerror(int st) {
@@ -593,6 +611,7 @@ static int validate_levels(int n_levels, const pasm_csr* A, const pasm_csr* M, c
 static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_csr* M, const pasm_csr* P) {
   c->nlev = n_levels;
   c->lv.resize((size_t)n_levels);
+  c->geo.assign((size_t)n_levels, std::array<int, PASM_TILE_N>{});
   const bool mixed = c->opts.precision == PASM_MIXED;
   for (int l = 0; l < n_levels; ++l) c->lv[(size_t)l].n = A[l].n_rows;
   for (int l = 0; l < n_levels; ++l) {
@@ -730,12 +749,131 @@ int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* 
   return PASM_OK;
 }
 
+extern "C++" {
+// Autotuner of the row-group kernels: for every level with at least
+// kTuneRows rows and every kernel kind of the context's precision, time each
+// valid number of 16-byte chunks per thread (1, 2, 4, 8) on the level's own
+// matrices (one warm-up, then the mean of three launches, CUDA events on the
+// context's stream) and keep the fastest.  Runs once per block width ldk; the
+// buffers it uses are scratch of the step (the update runs with no pair
+// selected, so U is read and rewritten unchanged).
+static constexpr int kTuneRows = 16384;
+
+template <typename Fn>
+static float time_launch(pasm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int geo, Fn&& fn) {
+  Launch L;
+  L.s = c->s;
+  L.geo = geo;
+  fn(L);
+  cudaEventRecord(e0, c->s);
+  for (int q = 0; q < 3; ++q) fn(L);
+  cudaEventRecord(e1, c->s);
+  if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms;
+}
+
+static int autotune(pasm_ctx* c) {
+  if (!c->opts.autotune || c->tuned_ldk == c->ldk) return PASM_OK;
+  for (auto& g : c->geo) g.fill(0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return PASM_ECUDA;
+  }
+  const bool mixed = c->opts.precision == PASM_MIXED;
+  const int ldk = c->ldk;
+  CK(cudaMemsetAsync(c->upd, 0, sizeof(int) * (size_t)ldk, c->s));
+  auto pick = [&](int l, int kind, int chunks, auto&& fn) {
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int ch : {1, 2, 4, 8}) {
+      if (chunks % ch != 0 || chunks / ch > 32) continue;
+      // the bordering kernel keeps its per-block reduction within 48 KB of shared memory
+      if (kind == PASM_TILE_BORDER && (size_t)(256 / (chunks / ch)) * 2 * ldk * sizeof(double) > 48 * 1024) continue;
+      const float ms = time_launch(c, e0, e1, ch, fn);
+      if (ms < best_ms) { best_ms = ms; best = ch; }
+    }
+    c->geo[(size_t)l][(size_t)kind] = best;
+  };
+  const int c32 = ldk / 4, c64 = ldk / 2;  // 16-byte chunks per row: float32, float64 / pairs
+  for (int l = 1; l < c->nlev; ++l) {
+    LevelDev& v = c->lv[(size_t)l];
+    LevelDev& w = c->lv[(size_t)l - 1];
+    if (v.n < kTuneRows) continue;
+    if (mixed) {
+      float *F = (float*)v.vF, *E = (float*)v.vE, *Tm = (float*)v.vT;
+      const float om = (float)c->opts.omega;
+      pick(l, PASM_TILE_JACOBI2_ZERO, c32, [&](const Launch& L) { jacobi2_zero<float>(L, v.A, v.dinv32, om, F, E, ldk); });
+      pick(l, PASM_TILE_JACOBI, c32,
+           [&](const Launch& L) { rowop<float>(L, OP_JACOBI, v.A, E, F, E, v.dinv32, om, Tm, ldk); });
+      pick(l, PASM_TILE_RESID_RESTRICT, c32,
+           [&](const Launch& L) { resid_restrict<float>(L, v.R, v.A, E, F, (float*)w.vF, ldk); });
+      pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
+        rowop<float>(L, OP_SPMM_ADD, v.P, (float*)w.vE, E, nullptr, nullptr, om, E, ldk);
+      });
+      pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
+        outer_rhs_residual_ff(L, v.A, v.M, c->lam, c->Uff, c->Fd, F, ldk);
+      });
+      pick(l, PASM_TILE_OUTER_RES, c64, [&](const Launch& L) { outer_residual_ff(L, v.A, c->Fd, c->X, F, ldk); });
+      pick(l, PASM_TILE_BORDER, c64, [&](const Launch& L) {
+        border_products_ff(L, v.A, v.M, c->X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
+      });
+      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) { spmm_ff(L, v.R, c->YA, true, w.BA, l - 1 >= 1, ldk); });
+      if (l < c->nlev - 1)
+        pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); });
+      const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
+      pick(l, PASM_TILE_UPDATE, c64, [&](const Launch& L) {
+        update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->U, ldk);
+      });
+    } else {
+      double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
+      const double om = c->opts.omega;
+      pick(l, PASM_TILE_JACOBI, c64, [&](const Launch& L) { rowop<double>(L, OP_JACOBI, v.A, E, F, E, v.dinv64, om, Tm, ldk); });
+      pick(l, PASM_TILE_RESID, c64,
+           [&](const Launch& L) { rowop<double>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk); });
+      pick(l, PASM_TILE_RESTRICT, c64, [&](const Launch& L) {
+        rowop<double>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (double*)w.vF, ldk);
+      });
+      pick(l, PASM_TILE_PROLONG, c64, [&](const Launch& L) {
+        rowop<double>(L, OP_SPMM_ADD, v.P, (double*)w.vE, E, nullptr, nullptr, om, E, ldk);
+      });
+      pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
+        outer_rhs_residual<double>(L, v.A, v.M, c->lam, c->U, c->Fd, F, ldk);
+      });
+      pick(l, PASM_TILE_OUTER_RES, c64, [&](const Launch& L) { outer_residual<double>(L, v.A, c->Fd, c->X, F, ldk); });
+      pick(l, PASM_TILE_BORDER, c64, [&](const Launch& L) {
+        border_products(L, v.A, v.M, c->X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
+      });
+      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) {
+        rowop<double>(L, OP_SPMM, v.R, c->YA, nullptr, nullptr, nullptr, 0.0, w.BA, ldk);
+      });
+      if (l < c->nlev - 1)
+        pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) {
+          rowop<double>(L, OP_SPMM, v.P, w.BA, nullptr, nullptr, nullptr, 0.0, v.BA, ldk);
+        });
+      const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
+      pick(l, PASM_TILE_UPDATE, c64,
+           [&](const Launch& L) { update_pairs(L, v.P, wsrc, c->X, c->alpha, c->upd, c->U, ldk); });
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaGetLastError());
+  c->tuned_ldk = ldk;
+  return PASM_OK;
+}
+}  // extern "C++"
+
 int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0) {
   if (!c || k < 1 || k > 256 || !(tol >= 0.0)) return PASM_EINVAL;
   if ((lambda0 == nullptr) != (U0 == nullptr)) return PASM_EINVAL;
   if (!lambda0 && k > c->NH) return PASM_EK_TOO_BIG;
   Scope sc(c);
   int r = alloc_k(c, k);
+  if (!r) r = autotune(c);
   if (r) return r;
   c->tol = tol;
   const int nf = c->lv.back().n;
@@ -914,6 +1052,12 @@ int pasm_project(pasm_ctx* c, const double* b, const double* cc, double* bq, dou
   CK(cudaMemcpyAsync(&after, c->proj_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
   return after != before ? PASM_ETIMEOUT : PASM_OK;
+}
+
+int pasm_tiles(pasm_ctx* c, int level, int* chunks_per_thread) {
+  if (!c || !chunks_per_thread || level < 0 || level >= c->nlev) return PASM_EINVAL;
+  for (int q = 0; q < PASM_TILE_N; ++q) chunks_per_thread[q] = c->geo[(size_t)level][(size_t)q];
+  return PASM_OK;
 }
 
 int pasm_projection_kind(pasm_ctx* c, int* kind) {

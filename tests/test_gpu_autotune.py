@@ -1,0 +1,54 @@
+"""The tile autotuner: the shapes it picks are valid, and a context that uses
+them computes the same correction steps as one with the default shapes.
+
+Changing the number of columns a thread handles leaves every entry's own
+arithmetic (its gather order and operations) unchanged; only the per-block
+partial sums of the bordering dot products regroup, so eigenvalues agree to
+1e-13 and vectors to 1e-11 (relative), in both precisions.
+"""
+import numpy as np
+import pytest
+
+import meshgen as mg
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def pg():
+    from paper_1908_10251_gb300 import build
+    build.build()
+    import paper_1908_10251_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_tiles_match_default(pg, precision):
+    H = mg.build_hierarchy(2, 256, 16)   # finest level 65,025 rows: tuned
+    A = [lv.A for lv in H.levels]
+    M = [lv.M for lv in H.levels]
+    res = []
+    for tune in (1, 0):
+        opts = pg.pasm_default_opts(precision=precision, autotune=tune)
+        ctx = pg.pasm_setup(A, M, H.P, opts, torch.cuda.current_stream().cuda_stream)
+        pg.pasm_init(ctx, 32, 1e-12)
+        tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
+        assert all(v in (0, 1, 2, 4, 8) for v in tiles.values())
+        if not tune:
+            assert all(v == 0 for v in tiles.values())
+        assert all(v == 0 for v in pg.pasm_tiles(ctx, 1).values())   # 31 x 31: below the tuning size
+        for _ in range(3):
+            pg.pasm_step(ctx)
+        n = H.fine.n
+        lam = np.zeros(32)
+        U = np.zeros((n, 32))
+        pg.pasm_get(ctx, lam, U)
+        res.append((lam, U))
+    (l1, U1), (l0, U0) = res
+    assert np.max(np.abs(l1 - l0) / l0) < 1e-13
+    assert np.max(np.abs(U1 - U0)) / np.max(np.abs(U0)) < 1e-11
