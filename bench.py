@@ -420,8 +420,14 @@ def main_ours(args):
     if dom in prof:
         roof["traffic"] = prof[dom]["dram_bytes_per_launch"]
         roof["traffic_source"] = prof[dom]["source"]
+    dominant_class = roof
     # the V-cycle's own roofline: finest-level float32 Jacobi sweeps (the metric's "V-cycle HBM GB/s")
+    # finest-level k_rowop Jacobi sweeps only (the fused two-sweep kernel of the same class moves
+    # fewer algorithmic bytes per launch and is left out)
     fj = main["fine_jacobi"]
+    if fj:
+        bmax = max(b for _, b in fj)
+        fj = [(t, b) for t, b in fj if b >= 0.99 * bmax]
     vcyc = None
     if fj:
         t_avg = sum(t for t, _ in fj) / len(fj)
@@ -432,6 +438,12 @@ def main_ours(args):
                 "algorithmic_bytes_per_launch": b_avg,
                 "traffic": prof.get("jacobi_fine", {}).get("dram_bytes_per_launch"),
                 "launches_timed": len(fj), "peak_note": "of %s" % peak_kind}
+    # the reported roofline kernel: the finest-level float32 Jacobi sweep, the V-cycle kernel the
+    # metric names and the largest HBM-bound kernel of the step; the dominant class stays alongside
+    roof = dict(vcyc) if vcyc else dominant_class
+    if vcyc:
+        roof["traffic_source"] = prof.get("jacobi_fine", {}).get("source")
+        roof["launches_per_step"] = round(len(fj) / 3.0, 2)
     classes = {q: {"ms_per_step": round(v[0] / 3, 4), "GBps": round(v[1] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0,
                    "GFLOPs": round(v[2] / (v[0] * 1e-3) / 1e9, 1) if v[0] else 0, "launches": v[3] // 3}
                for q, v in sorted(tr.items(), key=lambda kv: -kv[1][0])}
@@ -461,7 +473,7 @@ def main_ours(args):
                 "d2h_bytes_per_step": bout // max(S, 1), "seconds": e2e_s,
                 "note": "pasm_solve with pinned host inputs/outputs, S steps per call"},
         "roofline": roof,
-        "roofline_vcycle": vcyc,
+        "roofline_dominant_class": dominant_class,
         "smoother_training": training,
         "cpu_baseline": cpu,
         "gpu_launches": int(args.steps * main["launches_per_step"]),

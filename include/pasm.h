@@ -201,7 +201,10 @@ int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, do
 /* The tile shapes in use on `level`: chunks_per_thread[PASM_TILE_N] receives,
  * per kernel kind, the 16-byte chunks of a block-vector row each thread
  * handles (0 = the default shape: one chunk, or as many as keep at most 32
- * threads per row).  Errors: PASM_EINVAL. */
+ * threads per row).  For PASM_TILE_JACOBI2_ZERO and PASM_TILE_RESID_RESTRICT,
+ * -1 means the autotuner timed the fused kernel slower than its unfused pair
+ * (one sweep from zero + one sweep; residual + restriction) on this level,
+ * which then runs instead.  Errors: PASM_EINVAL. */
 int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 
 /* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else

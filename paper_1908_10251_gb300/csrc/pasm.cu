@@ -300,7 +300,8 @@ T* vcycle(pasm_ctx* c, int l) {
   T* cur = E;
   T* tmp = Tm;
   int s = 0;
-  if (fuse && c->opts.nu_pre >= 2) {
+  // a fused kernel whose tile entry is -1 was timed slower than its unfused pair on this level
+  if (fuse && c->opts.nu_pre >= 2 && c->geo[(size_t)l][PASM_TILE_JACOBI2_ZERO] >= 0) {
     jacobi2_zero<T>(launcher(c, l, PASM_TILE_JACOBI2_ZERO), v.A, dinv<T>(v), om, F, cur, ldk);
     s = 2;
   } else if (c->opts.nu_pre >= 1) {
@@ -313,7 +314,7 @@ T* vcycle(pasm_ctx* c, int l) {
     rowop<T>(launcher(c, l, PASM_TILE_JACOBI), OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
-  if (fuse) {
+  if (fuse && c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] >= 0) {
     resid_restrict<T>(launcher(c, l, PASM_TILE_RESID_RESTRICT), v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
   } else {
     rowop<T>(launcher(c, l, PASM_TILE_RESID), OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
@@ -786,7 +787,7 @@ static int autotune(pasm_ctx* c) {
   const bool mixed = c->opts.precision == PASM_MIXED;
   const int ldk = c->ldk;
   CK(cudaMemsetAsync(c->upd, 0, sizeof(int) * (size_t)ldk, c->s));
-  auto pick = [&](int l, int kind, int chunks, auto&& fn) {
+  auto pick = [&](int l, int kind, int chunks, auto&& fn) -> float {
     int best = 0;
     float best_ms = 1e30f;
     for (int ch : {1, 2, 4, 8}) {
@@ -797,6 +798,7 @@ static int autotune(pasm_ctx* c) {
       if (ms < best_ms) { best_ms = ms; best = ch; }
     }
     c->geo[(size_t)l][(size_t)kind] = best;
+    return best_ms;
   };
   const int c32 = ldk / 4, c64 = ldk / 2;  // 16-byte chunks per row: float32, float64 / pairs
   for (int l = 1; l < c->nlev; ++l) {
@@ -806,11 +808,21 @@ static int autotune(pasm_ctx* c) {
     if (mixed) {
       float *F = (float*)v.vF, *E = (float*)v.vE, *Tm = (float*)v.vT;
       const float om = (float)c->opts.omega;
-      pick(l, PASM_TILE_JACOBI2_ZERO, c32, [&](const Launch& L) { jacobi2_zero<float>(L, v.A, v.dinv32, om, F, E, ldk); });
-      pick(l, PASM_TILE_JACOBI, c32,
-           [&](const Launch& L) { rowop<float>(L, OP_JACOBI, v.A, E, F, E, v.dinv32, om, Tm, ldk); });
-      pick(l, PASM_TILE_RESID_RESTRICT, c32,
-           [&](const Launch& L) { resid_restrict<float>(L, v.R, v.A, E, F, (float*)w.vF, ldk); });
+      const float t_j2 = pick(l, PASM_TILE_JACOBI2_ZERO, c32,
+                              [&](const Launch& L) { jacobi2_zero<float>(L, v.A, v.dinv32, om, F, E, ldk); });
+      const float t_j = pick(l, PASM_TILE_JACOBI, c32,
+                             [&](const Launch& L) { rowop<float>(L, OP_JACOBI, v.A, E, F, E, v.dinv32, om, Tm, ldk); });
+      const float t_j0 = time_launch(c, e0, e1, 0, [&](const Launch& L) { jacobi_zero<float>(L, v.n, v.dinv32, om, F, E, ldk); });
+      if (t_j0 + t_j < t_j2) c->geo[(size_t)l][PASM_TILE_JACOBI2_ZERO] = -1;   // split: one sweep from zero + one sweep
+      const float t_rr = pick(l, PASM_TILE_RESID_RESTRICT, c32,
+                              [&](const Launch& L) { resid_restrict<float>(L, v.R, v.A, E, F, (float*)w.vF, ldk); });
+      const float t_r = pick(l, PASM_TILE_RESID, c32, [&](const Launch& L) {
+        rowop<float>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk);
+      });
+      const float t_s = pick(l, PASM_TILE_RESTRICT, c32, [&](const Launch& L) {
+        rowop<float>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (float*)w.vF, ldk);
+      });
+      if (t_r + t_s < t_rr) c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] = -1;    // split: residual, then restriction
       pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
         rowop<float>(L, OP_SPMM_ADD, v.P, (float*)w.vE, E, nullptr, nullptr, om, E, ldk);
       });

@@ -3,8 +3,11 @@ them computes the same correction steps as one with the default shapes.
 
 Changing the number of columns a thread handles leaves every entry's own
 arithmetic (its gather order and operations) unchanged; only the per-block
-partial sums of the bordering dot products regroup, so eigenvalues agree to
-1e-13 and vectors to 1e-11 (relative), in both precisions.
+partial sums of the bordering dot products regroup, so in float64 eigenvalues
+agree to 1e-13 and vectors to 1e-11 (relative).  In mixed precision the tuner
+may also replace a fused float32 multigrid kernel by its unfused pair, whose
+float32 roundings differ; the float64-accuracy outer iteration absorbs that to
+well below the float32 level (eigenvalues 1e-7, vectors 1e-5 after 3 steps).
 """
 import numpy as np
 import pytest
@@ -38,7 +41,8 @@ def test_autotuned_tiles_match_default(pg, precision):
         ctx = pg.pasm_setup(A, M, H.P, opts, torch.cuda.current_stream().cuda_stream)
         pg.pasm_init(ctx, 32, 1e-12)
         tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
-        assert all(v in (0, 1, 2, 4, 8) for v in tiles.values())
+        assert all(v in (-1, 0, 1, 2, 4, 8) for v in tiles.values())
+        assert all(v >= 0 for kk, v in tiles.items() if kk not in ("jacobi2_zero", "resid_restrict"))
         if not tune:
             assert all(v == 0 for v in tiles.values())
         assert all(v == 0 for v in pg.pasm_tiles(ctx, 1).values())   # 31 x 31: below the tuning size
@@ -50,5 +54,6 @@ def test_autotuned_tiles_match_default(pg, precision):
         pg.pasm_get(ctx, lam, U)
         res.append((lam, U))
     (l1, U1), (l0, U0) = res
-    assert np.max(np.abs(l1 - l0) / l0) < 1e-13
-    assert np.max(np.abs(U1 - U0)) / np.max(np.abs(U0)) < 1e-11
+    tl, tu = (1e-13, 1e-11) if precision == 0 else (1e-7, 1e-5)
+    assert np.max(np.abs(l1 - l0) / l0) < tl
+    assert np.max(np.abs(U1 - U0)) / np.max(np.abs(U0)) < tu
