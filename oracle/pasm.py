@@ -10,6 +10,9 @@ notes of the repository):
   * multigrid for the boundary value problem of Algorithm 1 step 1 = V-cycles
     with damped Jacobi smoothing (omega = 2/3, nu_pre = nu_post = 2), exact
     solve on the coarsest level V_H, two V-cycles per correction step;
+    optionally the paper's own smoother of Section 5.1, conjugate gradients
+    (nu_pre / nu_post CG steps, unpreconditioned, restarted at every
+    smoothing, each column its own CG);
   * the multigrid initial guess is the current eigenvector u^(l) (the
     contraction assumption of Theorem 3.1 measures from it);
   * initial pairs: the k smallest coarse eigenpairs of (A_H, M_H) prolongated
@@ -53,6 +56,7 @@ class Problem:
     nn_weights: object = None
     grids: object = None
     nn_bf16: bool = False          # round layer-2 inputs to bfloat16 (tensor-core path)
+    smoother: str = "jacobi"       # "jacobi" (damped Jacobi) or "cg" (conjugate gradients)
 
     def __post_init__(self):
         self.L = len(self.A) - 1
@@ -103,7 +107,8 @@ def sub_problem(prob: Problem, l: int) -> Problem:
     """The hierarchy truncated at level l (V_H = level 0 stays the coarse space)."""
     return Problem(prob.A[:l + 1], prob.M[:l + 1], prob.P[:l], omega=prob.omega, nu_pre=prob.nu_pre,
                    nu_post=prob.nu_post, cycles=prob.cycles, score=prob.score, nn_weights=prob.nn_weights,
-                   grids=None if prob.grids is None else prob.grids[:l + 1], nn_bf16=prob.nn_bf16)
+                   grids=None if prob.grids is None else prob.grids[:l + 1], nn_bf16=prob.nn_bf16,
+                   smoother=prob.smoother)
 
 
 def initial_state_nested(prob: Problem, k: int):
@@ -127,6 +132,34 @@ def jacobi(A, dinv, f, x, omega, nu):
     return x
 
 
+def cg(A, f, x, nu):
+    """nu conjugate-gradient steps for A x = f started from x, each column an
+    independent CG (Hestenes-Stiefel recurrences: residual r, direction p,
+    step alpha = r.r / p.A p, then beta = r'.r' / r.r).  A column whose
+    residual or curvature p.A p vanishes takes no step (alpha = beta = 0)."""
+    r = f - A @ x
+    p = r.copy()
+    rr = np.einsum("ij,ij->j", r, r)
+    for _ in range(nu):
+        q = A @ p
+        pq = np.einsum("ij,ij->j", p, q)
+        alpha = np.divide(rr, pq, out=np.zeros_like(rr), where=pq > 0)
+        x = x + alpha[None, :] * p
+        r = r - alpha[None, :] * q
+        rr_new = np.einsum("ij,ij->j", r, r)
+        beta = np.divide(rr_new, rr, out=np.zeros_like(rr), where=rr > 0)
+        p = r + beta[None, :] * p
+        rr = rr_new
+    return x
+
+
+def smooth(prob: Problem, l: int, f, x, nu):
+    """nu smoothing steps on level l with the problem's smoother."""
+    if prob.smoother == "cg":
+        return cg(prob.A[l], f, x, nu)
+    return jacobi(prob.A[l], prob.dinv[l], f, x, prob.omega, nu)
+
+
 def vcycle(prob: Problem, l: int, f, x):
     """One multigrid V-cycle for A_l x = f on level l: pre-smooth, restrict the
     residual with P^T, recurse from a zero guess, prolongate and correct,
@@ -134,7 +167,7 @@ def vcycle(prob: Problem, l: int, f, x):
     if l == 0:
         return sla.cho_solve(prob._chol_H, f)
     A, dinv, P = prob.A[l], prob.dinv[l], prob.P[l - 1]
-    x = jacobi(A, dinv, f, x, prob.omega, prob.nu_pre)
+    x = smooth(prob, l, f, x, prob.nu_pre)
     fc = P.T @ (f - A @ x)
     ec = vcycle(prob, l - 1, fc, np.zeros_like(fc))
     x = x + P @ ec
@@ -142,7 +175,7 @@ def vcycle(prob: Problem, l: int, f, x):
     if prob.nn_weights is not None and prob.grids is not None and prob.grids[l] and nu >= 1:
         x = learned_sweep(prob, l, f, x)
         nu -= 1
-    x = jacobi(A, dinv, f, x, prob.omega, nu)
+    x = smooth(prob, l, f, x, nu)
     return x
 
 
