@@ -176,13 +176,16 @@ def time_to_target(reach, refset, cap):
 
 # ----------------------------------------------------------------------------- our arm
 
-def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, nn_weights=None, init=0):
+def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, nn_weights=None, init=0,
+             smoother=None):
     k = WORK["k"]
     stream = torch.cuda.current_stream()
     A = [lv.A for lv in H.levels]
     M = [lv.M for lv in H.levels]
     t0 = time.perf_counter()
-    opts = pg.pasm_default_opts(precision=precision, smoother=1 if nn_weights is not None else 0, init=init)
+    if smoother is None:
+        smoother = 1 if nn_weights is not None else 0
+    opts = pg.pasm_default_opts(precision=precision, smoother=smoother, init=init)
     ctx = pg.pasm_setup(A, M, H.P, opts, stream.cuda_stream)
     if nn_weights is not None:
         pg.pasm_nn_setup(ctx, grid_widths(H), nn_weights)
@@ -381,6 +384,8 @@ def main_ours(args):
     for name, prec in modes:
         res[name] = run_mode(pg, torch, H, ref, prec, args.steps, args.warmup, rank, args.calib_steps)
     res["mixed_nested"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps, init=1)
+    # the smoother of the paper's experiments (Section 5.1): 2 CG steps pre and post
+    res["mixed_cg"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps, smoother=2)
     training = None
     if args.learned:
         w, train_s, losses = train_smoother(pg, torch, H)

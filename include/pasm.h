@@ -62,7 +62,7 @@ enum {
 enum { PASM_FP64 = 0, PASM_MIXED = 1 };           /* precision of the V-cycles   */
 enum { PASM_SCORE_A = 0, PASM_SCORE_B = 1 };      /* normalisation in the score  */
 enum { PASM_INIT_COARSE = 0, PASM_INIT_NESTED = 1 };
-enum { PASM_JACOBI = 0, PASM_LEARNED = 1 };       /* post-smoother               */
+enum { PASM_JACOBI = 0, PASM_LEARNED = 1, PASM_CG = 2 };  /* multigrid smoother     */
 enum { PASM_PROJ_TENSOR = 0, PASM_PROJ_FP64 = 1 };  /* coarse projection product */
 
 /* Kernel kinds whose tile shape the autotuner chooses (see pasm_tiles). */
@@ -111,10 +111,14 @@ typedef struct {
                           every intermediate level (Algorithm 2 step 2(A))
                           [PASM_INIT_COARSE]                                     */
   int use_graph;       /* capture the finest-level step in a CUDA graph [1]      */
-  int smoother;        /* PASM_JACOBI, or PASM_LEARNED: on levels given a grid by
-                          pasm_nn_setup the first post-smoothing sweep is the
-                          learned step with a per-pair Jacobi fallback (mixed
-                          precision only) [PASM_JACOBI]                        */
+  int smoother;        /* PASM_JACOBI (damped Jacobi sweeps); PASM_CG: nu_pre /
+                          nu_post conjugate-gradient steps, each pair its own
+                          unpreconditioned CG restarted at every smoothing (the
+                          smoother of the paper's experiments, Section 5.1);
+                          PASM_LEARNED: on levels given a grid by pasm_nn_setup
+                          the first post-smoothing sweep is the learned step
+                          with a per-pair Jacobi fallback (mixed precision
+                          only) [PASM_JACOBI]                                   */
   int projection;      /* PASM_PROJ_TENSOR: the dense coarse products Q^T b,
                           Q^T c and Q g run on the tensor cores (tcgen05) in
                           exact digit planes, added exactly and rounded once
@@ -243,6 +247,7 @@ enum {
   PASM_KC_CAST,         /* precision conversion                                   */
   PASM_KC_NN,           /* learned smoother (convolutions, training, fallback)    */
   PASM_KC_PROJ,         /* coarse projections Q^T b, Q^T c, Q g on tensor cores   */
+  PASM_KC_CG,           /* conjugate-gradient smoothing (vectors and scalars)     */
   PASM_KC_N
 };
 

@@ -14,5 +14,5 @@ from .capi import (  # noqa: F401
     pasm_nn_capture_residuals, pasm_nn_accepted, pasm_nn_errors,
     pasm_batch_setup, pasm_batch_solve, pasm_batch_destroy,
     PasmError, load_library,
-    PASM_PROJ_TENSOR, PASM_PROJ_FP64, PASM_FP64, PASM_MIXED, PASM_ETIMEOUT,
+    PASM_PROJ_TENSOR, PASM_PROJ_FP64, PASM_FP64, PASM_MIXED, PASM_ETIMEOUT, PASM_JACOBI, PASM_CG,
 )

@@ -25,7 +25,7 @@ PASM_PAIR_ACTIVE, PASM_PAIR_CONVERGED, PASM_PAIR_DEGENERATE, PASM_PAIR_NAN = 0, 
 PASM_FP64, PASM_MIXED = 0, 1
 PASM_SCORE_A, PASM_SCORE_B = 0, 1
 PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
-PASM_JACOBI, PASM_LEARNED = 0, 1
+PASM_JACOBI, PASM_LEARNED, PASM_CG = 0, 1, 2
 PASM_PROJ_TENSOR, PASM_PROJ_FP64 = 0, 1
 TILE_KINDS = ("jacobi", "jacobi2_zero", "resid_restrict", "resid", "restrict", "prolong", "outer_rhs",
               "outer_res", "border", "chain_r", "chain_p", "update")
@@ -256,7 +256,7 @@ def pasm_last_launches(ctx: Context) -> int:
     return n.value
 
 
-PASM_KC_N = 18
+PASM_KC_N = 19
 
 
 def pasm_trace_step(ctx: Context):

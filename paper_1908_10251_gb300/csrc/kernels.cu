@@ -673,3 +673,234 @@ void cast_d2f(const Launch& L, const double* in, float* out, int64_t count) {
 }
 
 }  // namespace pasm
+
+namespace pasm {
+
+// ----------------------------------------------------------------------------------------------
+// Conjugate-gradient smoother (the multigrid smoother of the paper's experiments, Section 5.1):
+// nu CG steps for A x = f, each column an independent CG, all columns batched.  Vectors in the
+// cycle's precision T; the column dot products are summed per thread in T, per block in float64
+// and across blocks in float64 by one block per column (fixed order: deterministic).
+namespace {
+
+// Per-block column sums s[c][v] (per thread) -> partial[blockIdx.x][col] in float64.
+template <typename T, int CH>
+__device__ __forceinline__ void block_column_partials(const T (&s)[CH][Vec16<T>::N], double* red, int grp,
+                                                      int lane, int tpr, int rpb, int ldk, double* partial) {
+  constexpr int V = Vec16<T>::N;
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) red[grp * ldk + (c * tpr + lane) * V + v] = (double)s[c][v];
+  __syncthreads();
+  for (int t = threadIdx.x; t < ldk; t += blockDim.x) {
+    double a = 0.0;
+    for (int r = 0; r < rpb; ++r) a += red[r * ldk + t];
+    partial[(size_t)blockIdx.x * ldk + t] = a;
+  }
+}
+
+// r = f - A x (x == nullptr: r = f), p = r, partial sums of r.r
+template <typename T, int CH>
+__global__ void __launch_bounds__(kBlock) k_cg_start(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                      const T* __restrict__ av, const T* __restrict__ X,
+                                                      const T* __restrict__ F, T* __restrict__ R, T* __restrict__ P,
+                                                      double* __restrict__ partial, int ldk, int tpr) {
+  extern __shared__ double red[];
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr, grp = threadIdx.x / tpr, lane = threadIdx.x % tpr;
+  T s[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) s[c][v] = T(0);
+  for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
+    T acc[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[c][v] = T(0);
+    if (X) gather_rows<T, CH>(ci, av, nullptr, T(0), X, rp[row], rp[row + 1], lane, tpr, ldk, acc);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const size_t off = base + (c * tpr + lane) * V;
+      T f[V], r[V];
+      ldg16<T>(F + off, f);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        r[v] = f[v] - acc[c][v];
+        s[c][v] = fma(r[v], r[v], s[c][v]);
+      }
+      Vec16<T>::store(R + off, r);
+      Vec16<T>::store(P + off, r);
+    }
+  }
+  block_column_partials<T, CH>(s, red, grp, lane, tpr, rpb, ldk, partial);
+}
+
+// q = A p, partial sums of p.q
+template <typename T, int CH>
+__global__ void __launch_bounds__(kBlock) k_cg_dir(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                    const T* __restrict__ av, const T* __restrict__ P,
+                                                    T* __restrict__ Q, double* __restrict__ partial, int ldk,
+                                                    int tpr) {
+  extern __shared__ double red[];
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr, grp = threadIdx.x / tpr, lane = threadIdx.x % tpr;
+  T s[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) s[c][v] = T(0);
+  for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
+    T acc[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) acc[c][v] = T(0);
+    gather_rows<T, CH>(ci, av, nullptr, T(0), P, rp[row], rp[row + 1], lane, tpr, ldk, acc);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const size_t off = base + (c * tpr + lane) * V;
+      T p[V];
+      ldg16<T>(P + off, p);
+#pragma unroll
+      for (int v = 0; v < V; ++v) s[c][v] = fma(p[v], acc[c][v], s[c][v]);
+      Vec16<T>::store(Q + off, acc[c]);
+    }
+  }
+  block_column_partials<T, CH>(s, red, grp, lane, tpr, rpb, ldk, partial);
+}
+
+// x = (x_zero ? 0 : x) + alpha p, r -= alpha q, partial sums of r.r
+template <typename T, int CH>
+__global__ void __launch_bounds__(kBlock) k_cg_update(int n, T* __restrict__ X, T* __restrict__ R,
+                                                       const T* __restrict__ P, const T* __restrict__ Q,
+                                                       const double* __restrict__ alpha, double* __restrict__ partial,
+                                                       int ldk, int tpr, int x_zero) {
+  extern __shared__ double red[];
+  constexpr int V = Vec16<T>::N;
+  const int rpb = kBlock / tpr, grp = threadIdx.x / tpr, lane = threadIdx.x % tpr;
+  T s[CH][V], a[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      s[c][v] = T(0);
+      a[c][v] = (T)alpha[(c * tpr + lane) * V + v];
+    }
+  for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const size_t off = base + (c * tpr + lane) * V;
+      T x[V], r[V], p[V], q[V];
+      if (x_zero) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = T(0);
+      } else {
+        Vec16<T>::load(X + off, x);
+      }
+      Vec16<T>::load(R + off, r);
+      ldg16<T>(P + off, p);
+      ldg16<T>(Q + off, q);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        x[v] = fma(a[c][v], p[v], x[v]);
+        r[v] = fma(-a[c][v], q[v], r[v]);
+        s[c][v] = fma(r[v], r[v], s[c][v]);
+      }
+      Vec16<T>::store(X + off, x);
+      Vec16<T>::store(R + off, r);
+    }
+  }
+  block_column_partials<T, CH>(s, red, grp, lane, tpr, rpb, ldk, partial);
+}
+
+// p = r + beta p
+template <typename T>
+__global__ void k_cg_pupdate(int64_t total, int ldk, const T* __restrict__ R, T* __restrict__ P,
+                             const double* __restrict__ beta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    P[i] = fma((T)beta[i % ldk], P[i], R[i]);
+}
+
+// One block per column: s = sum of the partials; mode 0: rr = s; mode 1: alpha = rr / s
+// (0 if s <= 0); mode 2: beta = s / rr (0 if rr <= 0), rr = s.
+__global__ void __launch_bounds__(128) k_cg_scalar(const double* __restrict__ partial, int nblk, int ldk, int mode,
+                                                   double* __restrict__ rr, double* __restrict__ coef) {
+  __shared__ double w[4];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 128) s += partial[(size_t)b * ldk + c];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = (w[0] + w[1]) + (w[2] + w[3]);
+    if (mode == 0) {
+      rr[c] = s;
+    } else if (mode == 1) {
+      coef[c] = s > 0.0 ? rr[c] / s : 0.0;
+    } else {
+      coef[c] = rr[c] > 0.0 ? s / rr[c] : 0.0;
+      rr[c] = s;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void cg_smooth(const Launch& L, const DCsr& A, const T* F, T* X, bool x_zero, T* R, T* P, T* Q, const CgWork& w,
+               int ldk, int nu) {
+  if (A.n_rows == 0 || nu < 1) return;
+  const Geo g = geometry<T>(ldk, L.geo);
+  const int rpb = kBlock / g.tpr;
+  const int grid = std::max(1, std::min((A.n_rows + rpb - 1) / rpb, w.max_blocks));
+  const size_t smem = (size_t)rpb * ldk * sizeof(double);
+  const double sz = sizeof(T), rows = A.n_rows, nnz = (double)A.nnz, vec = rows * ldk * sz;
+  const double mat = nnz * (4.0 + sz) + (rows + 1) * 4.0;
+  const T* av = vals<T>(A);
+  auto scalars = [&](int mode, double* coef) {
+    L.begin(KC_CG, (double)grid * ldk * 8.0, (double)grid * ldk);
+    k_cg_scalar<<<ldk, 128, 0, L.s>>>(w.partial, grid, ldk, mode, w.rr, coef);
+    L.bump();
+  };
+  L.rows(A.n_rows);
+  L.begin(KC_CG, (x_zero ? 0.0 : mat + vec) + 3.0 * vec, x_zero ? 2.0 * rows * ldk : 2.0 * nnz * ldk + 3.0 * rows * ldk);
+  PASM_DISPATCH_CH(g.ch, k_cg_start<T, CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, av, x_zero ? nullptr : X,
+                                                                         F, R, P, w.partial, ldk, g.tpr));
+  L.bump();
+  scalars(0, nullptr);
+  for (int it = 0; it < nu; ++it) {
+    L.rows(A.n_rows);
+    L.begin(KC_CG, mat + 2.0 * vec, 2.0 * nnz * ldk + 2.0 * rows * ldk);
+    PASM_DISPATCH_CH(g.ch, k_cg_dir<T, CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, av, P, Q, w.partial,
+                                                                         ldk, g.tpr));
+    L.bump();
+    scalars(1, w.alpha);
+    const bool xz = x_zero && it == 0;
+    L.rows(A.n_rows);
+    L.begin(KC_CG, (xz ? 5.0 : 6.0) * vec, 6.0 * rows * ldk);
+    PASM_DISPATCH_CH(g.ch, k_cg_update<T, CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, X, R, P, Q, w.alpha, w.partial,
+                                                                            ldk, g.tpr, xz ? 1 : 0));
+    L.bump();
+    if (it + 1 < nu) {
+      scalars(2, w.beta);
+      const int64_t total = (int64_t)A.n_rows * ldk;
+      L.begin(KC_CG, 3.0 * vec, 2.0 * rows * ldk);
+      k_cg_pupdate<T><<<(int)std::min<int64_t>((total + kBlock - 1) / kBlock, 152 * 16), kBlock, 0, L.s>>>(
+          total, ldk, R, P, w.beta);
+      L.bump();
+    }
+  }
+}
+template void cg_smooth<float>(const Launch&, const DCsr&, const float*, float*, bool, float*, float*, float*,
+                               const CgWork&, int, int);
+template void cg_smooth<double>(const Launch&, const DCsr&, const double*, double*, bool, double*, double*, double*,
+                                const CgWork&, int, int);
+
+}  // namespace pasm

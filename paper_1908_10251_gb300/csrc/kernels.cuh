@@ -25,7 +25,7 @@ template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
 // Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
 enum KernelClass {
   KC_JACOBI = 0, KC_JACOBI0, KC_RESID, KC_SPMM, KC_PROLONG, KC_DENSE, KC_OUTER_RHS, KC_OUTER_RES, KC_AXPY,
-  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_PROJ, KC_N
+  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_PROJ, KC_CG, KC_N
 };
 
 // Host-side event recorder (defined in pasm.cu); null when not tracing.
@@ -130,6 +130,20 @@ void update_pairs(const Launch& L, const DCsr& P, const double* W, const double*
 // Same with P = identity (single-level hierarchy): U = alpha X + W.
 void update_pairs_identity(const Launch& L, int n, const double* W, const double* X, const double* alpha,
                            const int* upd, double* U, int ldk);
+
+// ----------------------------------------------------------------------------------------------
+// Conjugate-gradient smoothing (kernels.cu): nu CG steps for A x = F, every
+// column its own CG.  x_zero: start from x = 0 (X is written, not read).
+// R, P, Q are n x ldk scratch blocks; the work arrays hold per-block partial
+// sums (max_blocks x ldk) and the per-column scalars r.r, alpha, beta.
+struct CgWork {
+  double* partial = nullptr;
+  int max_blocks = 0;
+  double *rr = nullptr, *alpha = nullptr, *beta = nullptr;
+};
+template <typename T>
+void cg_smooth(const Launch& L, const DCsr& A, const T* F, T* X, bool x_zero, T* R, T* P, T* Q, const CgWork& w,
+               int ldk, int nu);
 
 // ----------------------------------------------------------------------------------------------
 // Double-float versions of the float64-accuracy kernels (ff.cu), used in mixed

@@ -64,6 +64,8 @@ struct LevelDev {
   void* vT = nullptr;  // V-cycle temporary
   double* BA = nullptr;  // float64 chain buffers (restriction of A u~, prolongation of u_H)
   double* BM = nullptr;  // float64 chain buffer (restriction of M u~)
+  void* vP = nullptr;    // CG smoothing: search directions and their images (cycle precision)
+  void* vQ = nullptr;
 };
 
 }  // namespace
@@ -119,6 +121,7 @@ struct pasm_ctx {
   int* proj_err = nullptr;                 // timed-out tensor-core waits of the projection kernel
   unsigned long long* proj_hl = nullptr;   // integer sums of the projection (k-dependent scratch)
   unsigned int* proj_tickets = nullptr;
+  CgWork cg;                               // CG smoothing: partial sums and per-column scalars
   // autotuned row-group geometry per level and kernel kind (0 = default), for block width tuned_ldk
   std::vector<std::array<int, PASM_TILE_N>> geo;
   int tuned_ldk = 0;
@@ -300,8 +303,14 @@ T* vcycle(pasm_ctx* c, int l) {
   T* cur = E;
   T* tmp = Tm;
   int s = 0;
+  const bool cg = c->opts.smoother == PASM_CG;
   // a fused kernel whose tile entry is -1 was timed slower than its unfused pair on this level
-  if (fuse && c->opts.nu_pre >= 2 && c->geo[(size_t)l][PASM_TILE_JACOBI2_ZERO] >= 0) {
+  if (cg && c->opts.nu_pre >= 1) {
+    cg_smooth<T>(L, v.A, F, cur, true, tmp, (T*)v.vP, (T*)v.vQ, c->cg, ldk, c->opts.nu_pre);
+    s = c->opts.nu_pre;
+  } else if (cg) {
+    cudaMemsetAsync(cur, 0, sizeof(T) * (size_t)v.n * ldk, c->s);
+  } else if (fuse && c->opts.nu_pre >= 2 && c->geo[(size_t)l][PASM_TILE_JACOBI2_ZERO] >= 0) {
     jacobi2_zero<T>(launcher(c, l, PASM_TILE_JACOBI2_ZERO), v.A, dinv<T>(v), om, F, cur, ldk);
     s = 2;
   } else if (c->opts.nu_pre >= 1) {
@@ -323,6 +332,10 @@ T* vcycle(pasm_ctx* c, int l) {
   }
   T* ec = vcycle<T>(c, l - 1);
   rowop<T>(launcher(c, l, PASM_TILE_PROLONG), OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
+  if (cg) {
+    cg_smooth<T>(L, v.A, F, cur, false, tmp, (T*)v.vP, (T*)v.vQ, c->cg, ldk, c->opts.nu_post);
+    return cur;
+  }
   s = 0;
   if (Fused<T>::on) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
   if (s == 1) std::swap(cur, tmp);
@@ -457,7 +470,7 @@ void free_k(pasm_ctx* c) {
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   for (void* p : c->kallocs) cudaFree(p);
   c->kallocs.clear();
-  for (auto& v : c->lv) { v.vF = v.vE = v.vT = nullptr; v.BA = v.BM = nullptr; }
+  for (auto& v : c->lv) { v.vF = v.vE = v.vT = nullptr; v.BA = v.BM = nullptr; v.vP = v.vQ = nullptr; }
   c->initialized = false;
   c->k = 0;
 }
@@ -486,6 +499,10 @@ int alloc_k(pasm_ctx* c, int k) {
       v.vF = a; v.vE = b; v.vT = t;
     }
     if (l < c->nlev - 1) { AL(K, &v.BA, m); AL(K, &v.BM, m); }
+    if (c->opts.smoother == PASM_CG && l >= 1) {
+      if (mixed) { float *p, *q; AL(K, &p, m); AL(K, &q, m); v.vP = p; v.vQ = q; }
+      else { double *p, *q; AL(K, &p, m); AL(K, &q, m); v.vP = p; v.vQ = q; }
+    }
   }
   const size_t nh = (size_t)c->NH * ldk;
   AL(K, &c->lam, ldk); AL(K, &c->lam2, ldk); AL(K, &c->alpha, ldk); AL(K, &c->bz, 2 * ldk);
@@ -494,6 +511,11 @@ int alloc_k(pasm_ctx* c, int k) {
   AL(K, &c->active, ldk); AL(K, &c->upd, ldk); AL(K, &c->steps, ldk); AL(K, &c->status, ldk);
   AL(K, &c->active2, ldk); AL(K, &c->steps2, ldk); AL(K, &c->status2, ldk);
   AL(K, &c->nact, 1); AL(K, &c->diag, 8);
+  if (c->opts.smoother == PASM_CG) {
+    c->cg.max_blocks = 152 * 8;
+    AL(K, &c->cg.partial, (size_t)c->cg.max_blocks * ldk);
+    AL(K, &c->cg.rr, ldk); AL(K, &c->cg.alpha, ldk); AL(K, &c->cg.beta, ldk);
+  }
   if (c->proj_tc) {
     const size_t words = proj_scratch_words(c->NH, 2 * ldk), tickets = proj_tickets(c->NH, 2 * ldk);
     AL(K, &c->proj_hl, words); AL(K, &c->proj_tickets, tickets);
@@ -726,7 +748,7 @@ int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* 
       (o.precision != PASM_FP64 && o.precision != PASM_MIXED) ||
       (o.score_norm != PASM_SCORE_A && o.score_norm != PASM_SCORE_B) ||
       (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED) ||
-      (o.smoother != PASM_JACOBI && o.smoother != PASM_LEARNED) ||
+      (o.smoother != PASM_JACOBI && o.smoother != PASM_LEARNED && o.smoother != PASM_CG) ||
       (o.smoother == PASM_LEARNED && o.precision != PASM_MIXED) ||
       (o.projection != PASM_PROJ_TENSOR && o.projection != PASM_PROJ_FP64))
     return PASM_EINVAL;
@@ -1323,7 +1345,7 @@ int pasm_trace_launches(pasm_ctx* c, int max, int* cls, int* rows, float* ms, do
 const char* pasm_kernel_class_name(int cls) {
   static const char* names[KC_N] = {"jacobi", "jacobi0", "resid", "spmm", "prolong", "dense", "outer_rhs",
                                     "outer_res", "axpy", "border", "colsum", "init", "secular", "update",
-                                    "count", "cast", "nn", "proj"};
+                                    "count", "cast", "nn", "proj", "cg"};
   return (cls >= 0 && cls < KC_N) ? names[cls] : "unknown";
 }
 
