@@ -34,6 +34,7 @@ import scipy.sparse as sp
 __all__ = [
     "Level", "Hierarchy", "reference_simplices", "assemble", "interpolation",
     "build_hierarchy", "gaussian_log_field", "continuous_eigenvalues",
+    "assemble_operator", "element_averages", "example2_diffusion", "example2_potential",
 ]
 
 
@@ -161,6 +162,91 @@ def assemble(dim: int, N: int, kappa=None):
     return _stencil_to_csr(dim, N, Avals), _stencil_to_csr(dim, N, Mvals)
 
 
+# Degree-2 quadrature on a simplex: barycentric points and weights (fractions of
+# the volume).  Tetrahedron: the symmetric 4-point rule (a, b, b, b),
+# a = (5 + 3 sqrt 5) / 20, b = (5 - sqrt 5) / 20, exact for quadratics.
+# Triangle: the 3 edge midpoints, exact for quadratics.
+def _quadrature(dim: int):
+    if dim == 3:
+        a = (5.0 + 3.0 * np.sqrt(5.0)) / 20.0
+        b = (5.0 - np.sqrt(5.0)) / 20.0
+        pts = np.array([[a, b, b, b], [b, a, b, b], [b, b, a, b], [b, b, b, a]])
+        return pts, np.full(4, 0.25)
+    if dim == 2:
+        pts = np.array([[0.5, 0.5, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5]])
+        return pts, np.full(3, 1.0 / 3.0)
+    raise ValueError("dim must be 2 or 3")
+
+
+def element_averages(dim: int, N: int, diffusion):
+    """Per simplex type t and cell, the average of the diffusion tensor over the
+    simplex by the degree-2 rule (exact for quadratic entries): a list over t of
+    arrays of shape (N,)*dim + (dim, dim), and the simplex volume."""
+    h = 1.0 / N
+    pts, wts = _quadrature(dim)
+    cells = np.stack(np.meshgrid(*[np.arange(N)] * dim, indexing="ij"), axis=-1).astype(np.float64)
+    out = []
+    for offsets in reference_simplices(dim):
+        Xv = h * (cells[..., None, :] + offsets[None, :].astype(np.float64))   # (..., dim+1, dim)
+        xq = np.einsum("qv,...vd->...qd", pts, Xv)                             # (..., q, dim)
+        out.append(np.einsum("q,...qij->...ij", wts, diffusion(xq)))
+    vol = h ** dim / float(np.prod(np.arange(1, dim + 1)))
+    return out, vol
+
+
+def assemble_operator(dim: int, N: int, diffusion, potential=None):
+    """Stiffness A of a(u, v) = int grad v . D grad u + phi u v and the mass M of
+    P1 elements on the uniform mesh with h = 1/N (the general second-order
+    operator of the paper's Example 2, Section 5.2).
+
+    diffusion(x): D at points x (array (..., dim)) -> (..., dim, dim), symmetric
+    positive definite; potential(x) -> (...) or None.  Both element integrals
+    use the degree-2 rule of `_quadrature`: exact for D with quadratic entries
+    (so the stiffness part is exact) and for constant phi."""
+    h = 1.0 / N
+    pts, wts = _quadrature(dim)
+    cells = np.stack(np.meshgrid(*[np.arange(N)] * dim, indexing="ij"), axis=-1).astype(np.float64)
+    avgs, vol = element_averages(dim, N, diffusion)
+    Avals, Mvals = {}, {}
+    for t, offsets in enumerate(reference_simplices(dim)):
+        X = h * offsets.astype(np.float64)
+        B = (X[1:] - X[0]).T
+        Binv = np.linalg.inv(B)
+        G = np.zeros((dim + 1, dim))
+        G[1:] = Binv
+        G[0] = -Binv.sum(axis=0)
+        Kloc = vol * np.einsum("ai,...ij,bj->...ab", G, avgs[t], G)            # (..., dim+1, dim+1)
+        if potential is not None:
+            Xv = h * (cells[..., None, :] + offsets[None, :].astype(np.float64))
+            xq = np.einsum("qv,...vd->...qd", pts, Xv)
+            phi = potential(xq)                                                   # (..., q)
+            Kloc = Kloc + vol * np.einsum("q,...q,qa,qb->...ab", wts, phi, pts, pts)
+        Ml = vol / ((dim + 1) * (dim + 2)) * (np.ones((dim + 1, dim + 1)) + np.eye(dim + 1))
+        for a in range(dim + 1):
+            for b in range(dim + 1):
+                delta = tuple(int(x) for x in offsets[b] - offsets[a])
+                sl = tuple(slice(int(offsets[a][ax]), int(offsets[a][ax]) + N) for ax in range(dim))
+                for store, loc in ((Avals, Kloc[..., a, b]), (Mvals, Ml[a, b])):
+                    if delta not in store:
+                        store[delta] = np.zeros((N + 1,) * dim)
+                    store[delta][sl] += loc
+    Avals = {o: g for o, g in Avals.items() if np.any(g != 0.0)}
+    Mvals = {o: g for o, g in Mvals.items() if np.any(g != 0.0)}
+    return _stencil_to_csr(dim, N, Avals), _stencil_to_csr(dim, N, Mvals)
+
+
+def example2_diffusion(x):
+    """D(x) = I + (x - 1/2)(x - 1/2)^T (the paper's Example 2, Section 5.2)."""
+    y = x - 0.5
+    d = x.shape[-1]
+    return np.eye(d) + y[..., :, None] * y[..., None, :]
+
+
+def example2_potential(x):
+    """phi(x) = exp(prod_i (x_i - 1/2)) (the paper's Example 2, Section 5.2)."""
+    return np.exp(np.prod(x - 0.5, axis=-1))
+
+
 def interpolation(dim: int, N_fine: int) -> sp.csr_matrix:
     """Linear interpolation from the mesh with N_fine/2 cells per side to N_fine.
 
@@ -193,14 +279,17 @@ def interpolation(dim: int, N_fine: int) -> sp.csr_matrix:
     return P
 
 
-def build_hierarchy(dim: int, N_fine: int, N_coarse: int, kappa=None, galerkin: bool = False) -> Hierarchy:
+def build_hierarchy(dim: int, N_fine: int, N_coarse: int, kappa=None, galerkin: bool = False,
+                    operator=None) -> Hierarchy:
     """Nested hierarchy N_coarse, 2 N_coarse, ..., N_fine (every dyadic level).
 
     kappa: fine-level per-simplex coefficient (see `assemble`) or None.  With a
     variable kappa (or galerkin=True) the coarser A_l, M_l are the Galerkin
     products P^T A P, P^T M P, so that every level is a subspace restriction of
     the finest pencil; with kappa = 1 and galerkin=False each level is assembled
-    directly (the two agree to rounding because the spaces are nested)."""
+    directly (the two agree to rounding because the spaces are nested).
+    operator: (diffusion, potential) for `assemble_operator` on the finest
+    level (e.g. the paper's Example 2), coarser levels by Galerkin products."""
     if N_fine % N_coarse or (N_fine // N_coarse) & (N_fine // N_coarse - 1):
         raise ValueError("N_fine / N_coarse must be a power of two")
     Ns = []
@@ -210,10 +299,13 @@ def build_hierarchy(dim: int, N_fine: int, N_coarse: int, kappa=None, galerkin: 
         N //= 2
     Ns = Ns[::-1]
     Ps = [interpolation(dim, Nf) for Nf in Ns[1:]]
-    if kappa is None and not galerkin:
+    if kappa is None and not galerkin and operator is None:
         levels = [Level(dim, N, *assemble(dim, N)) for N in Ns]
     else:
-        Af, Mf = assemble(dim, Ns[-1], kappa)
+        if operator is not None:
+            Af, Mf = assemble_operator(dim, Ns[-1], *operator)
+        else:
+            Af, Mf = assemble(dim, Ns[-1], kappa)
         mats = [(Af, Mf)]
         for P in Ps[::-1]:
             A, M = mats[-1]
