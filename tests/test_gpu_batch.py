@@ -67,3 +67,62 @@ def test_kappa_problem_step_parity(pg):
     lg = np.zeros(k)
     pg.pasm_get(ctx, lg)
     assert np.allclose(lg, lam, rtol=1e-10)
+
+
+def test_uneven_batch_full_size(pg):
+    """The uneven batch at full size: 16 problems -div(kappa grad u) = lambda u,
+    kappa = exp(g_p) with g_p a seeded Gaussian field (sigma 1, correlation 0.1,
+    seed 1000 + p), fine grids 2^(8 + p mod 4) per side (65,025 to 4,190,209
+    DoF), k_p = (8, 16, 32, 64, 128)[p mod 5], H = 1/16, mixed precision, all
+    solved together by pasm_batch_solve (60 steps at most, tol 1e-10).
+
+    No oracle runs at these sizes; checked instead, in float64 on the CPU:
+      * every pair reported converged is a Ritz pair: its eigenvalue is the
+        Rayleigh quotient u^T A u / u^T M u of its vector (1e-9);
+      * pairs with relative residual ||A u - lambda M u|| / (lambda ||M u||)
+        below 1e-3 are eigenpairs: on the four 256^2 problems each is within
+        1e-9 of a shift-invert reference eigenvalue, and there are at least 60
+        in the batch.  (A residual norm amplifies the float32 V-cycles'
+        high-frequency error by up to lambda_max / lambda, so it is a coarse
+        test.)  The other converged pairs are the method's spurious freezes: with
+        this coarse space several pairs can select the same augmented Ritz pair,
+        whose value then stops changing, and the paper's |delta lambda| test
+        reads that as convergence -- the oracle freezes pairs 11-15 of problem 1
+        at the same 232.7311330 (residual 4) as the GPU does;
+      * problem 1 solved alone gives exactly what it gives in the batch."""
+    from oracle.reference import smallest_eigenvalues
+    probs, ks = [], []
+    for p in range(16):
+        N = 2 ** (8 + p % 4)
+        kap = mg.gaussian_log_field(N, 1000 + p)
+        probs.append(mg.build_hierarchy(2, N, 16, kappa=kap))
+        ks.append((8, 16, 32, 64, 128)[p % 5])
+    opts = pg.pasm_default_opts(precision=1, max_steps=60)
+    batch = pg.pasm_batch_setup([parts(H) for H in probs], opts, torch.cuda.current_stream().cuda_stream)
+    code, lams, Us, steps, stats, rounds = pg.pasm_batch_solve(batch, ks, 1e-10)
+    pg.pasm_batch_destroy(batch)
+    true_pairs = 0
+    for p, (H, k, lam, U, st) in enumerate(zip(probs, ks, lams, Us, stats)):
+        conv = st == 1
+        A, M = H.fine.A, H.fine.M
+        Uc = U[:, conv]
+        MU = M @ Uc
+        AU = A @ Uc
+        rq = np.einsum("ij,ij->j", Uc, AU) / np.einsum("ij,ij->j", Uc, MU)
+        assert np.max(np.abs(rq - lam[conv]) / lam[conv], initial=0.0) < 1e-9, p
+        res = np.linalg.norm(AU - MU * lam[conv][None, :], axis=0) / (lam[conv] * np.linalg.norm(MU, axis=0))
+        good = lam[conv][res < 1e-3]
+        true_pairs += good.size
+        if H.fine.N == 256:
+            ref = smallest_eigenvalues(A, M, k + 8)
+            err = np.array([np.min(np.abs(ref - v)) / v for v in good])
+            assert err.max(initial=0.0) < 1e-9, (p, float(err.max()))
+    assert true_pairs >= 60, true_pairs
+    # problem 1 alone
+    A, M, P = parts(probs[1])
+    ctx = pg.pasm_setup(A, M, P, opts, torch.cuda.current_stream().cuda_stream)
+    k = ks[1]
+    lam = np.zeros(k)
+    U = np.zeros((probs[1].fine.n, k))
+    pg.pasm_solve(ctx, k, 1e-10, None, None, lam, U, None, None)
+    assert np.array_equal(lam, lams[1]) and np.array_equal(U, Us[1])
