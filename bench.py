@@ -177,7 +177,7 @@ def time_to_target(reach, refset, cap):
 # ----------------------------------------------------------------------------- our arm
 
 def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, nn_weights=None, init=0,
-             smoother=None):
+             smoother=None, nn_widths=None):
     k = WORK["k"]
     stream = torch.cuda.current_stream()
     A = [lv.A for lv in H.levels]
@@ -188,7 +188,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
     opts = pg.pasm_default_opts(precision=precision, smoother=smoother, init=init)
     ctx = pg.pasm_setup(A, M, H.P, opts, stream.cuda_stream)
     if nn_weights is not None:
-        pg.pasm_nn_setup(ctx, grid_widths(H), nn_weights)
+        pg.pasm_nn_setup(ctx, grid_widths(H) if nn_widths is None else nn_widths, nn_weights)
     setup_s = time.perf_counter() - t0
     # cost of the start: a nested start (Algorithm 2 step 2(A)) runs correction steps on the
     # intermediate levels; it is timed as the difference to a coarse start of the same context
@@ -391,6 +391,11 @@ def main_ours(args):
         w, train_s, losses = train_smoother(pg, torch, H)
         res["mixed_learned"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps,
                                         nn_weights=w)
+        # the learned step only on the grids up to h = 4 h_fine (the two finest levels keep Jacobi)
+        coarse = grid_widths(H)
+        coarse[-2:] = 0
+        res["mixed_learned_coarse"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank,
+                                               args.calib_steps, nn_weights=w, nn_widths=coarse)
         training = {"seconds": train_s, "loss_first": losses[0], "loss_last": losses[-1]}
     primary, primary_prec = modes[0]
     main = res[primary]

@@ -111,6 +111,7 @@ struct pasm_ctx {
     double *partial = nullptr, *norms = nullptr, *loss = nullptr;
     int* accepted = nullptr;
     int* err = nullptr;                      // timed-out tensor-core waits
+    NNOuterWeights w13{};                    // host copy of layers 1 and 3 (kernel parameters)
     std::vector<void*> allocs;
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
@@ -277,7 +278,7 @@ int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
   NNGrid g{nn.nx[l], nn.ny[l], ldk, c->k};
   const float om = (float)c->opts.omega;
   rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, nn.R, ldk);        // r = f - A e
-  if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.W, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
+  if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.w13, nn.W, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
   else nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
   nn_add(L, (int64_t)v.n * ldk, cur, nn.D, nn.X);                                 // e + d
   rowop<float>(L, OP_RESID, v.A, nn.X, F, nullptr, nullptr, om, nn.Rt, ldk);      // f - A (e + d)
@@ -1164,6 +1165,16 @@ static int nn_ensure(pasm_ctx* c, int64_t pixpairs, int64_t vecs, bool backward)
   return PASM_OK;
 }
 
+// Copy layers 1 and 3 of the device weights into the host copy the
+// tensor-core forward passes as kernel parameters.
+static int nn_refresh_host_weights(pasm_ctx* c) {
+  std::vector<float> h((size_t)kNNWeights);
+  CK(cudaMemcpy(h.data(), c->nn.W, sizeof(float) * kNNWeights, cudaMemcpyDeviceToHost));
+  std::memcpy(c->nn.w13.w1, h.data(), sizeof(float) * 144);
+  std::memcpy(c->nn.w13.w3, h.data() + 144 + 2304, sizeof(float) * 144);
+  return PASM_OK;
+}
+
 int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
   if (!c || !nx || !weights) return PASM_EINVAL;
   if (c->opts.precision != PASM_MIXED) return PASM_EINVAL;
@@ -1189,6 +1200,7 @@ int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
     CK(cudaMemset(nn.err, 0, sizeof(int) * 4));
   }
   CK(cudaMemcpy(nn.W, weights, sizeof(float) * kNNWeights, cudaMemcpyDefault));
+  if (int rw = nn_refresh_host_weights(c)) return rw;
   CK(cudaMemset(nn.m, 0, sizeof(float) * kNNWeights));
   CK(cudaMemset(nn.v, 0, sizeof(float) * kNNWeights));
   CK(cudaMemset(nn.accepted, 0, sizeof(int) * 256));
@@ -1236,7 +1248,7 @@ int pasm_nn_apply(pasm_ctx* c, int level, int k, const float* R, float* D) {
   if (r) return r;
   NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
   if (c->opts.smoother == PASM_LEARNED && nn_tc_supported(ldk2))
-    nn_forward_tc(launcher(c), g, nn.W, nn.R, nn.D, nn.err);
+    nn_forward_tc(launcher(c), g, nn.w13, nn.W, nn.R, nn.D, nn.err);
   else
     nn_forward(launcher(c), g, nn.buf, nn.W, nn.R, nn.D);
   CK(cudaMemcpy2DAsync(D, sizeof(float) * k, nn.D, sizeof(float) * ldk2, sizeof(float) * k, n, cudaMemcpyDefault,
@@ -1293,7 +1305,10 @@ int pasm_nn_train(pasm_ctx* c, int level, int k, const float* R, int iters, floa
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
-  return PASM_OK;
+  // the tensor-core forward takes layers 1 and 3 as kernel parameters: refresh them and
+  // drop a captured step graph that holds the old values
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return nn_refresh_host_weights(c);
 }
 
 int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {

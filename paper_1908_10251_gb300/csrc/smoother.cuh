@@ -43,8 +43,16 @@ void nn_select(const Launch& L, int n, int ldk, const float* E, const float* D, 
 // Fused tensor-core forward (smoother_tc.cu): D = N(R) with layer 2 on tcgen05
 // (bf16 operands, float32 accumulation); needs ldk % 8 == 0.  A timed-out wait
 // increments *err and leaves D unwritten for that tile.
+// The CUDA-core weights of layers 1 (1 -> 16) and 3 (16 -> 1), passed by value
+// so that the kernel reads them from its parameter space; W (device) still
+// supplies layer 2.  A host copy must track every change of W.
+struct NNOuterWeights {
+  float w1[144];  // [tap][out]
+  float w3[144];  // [tap][in]
+};
 cudaError_t nn_tc_prepare();
 bool nn_tc_supported(int ldk);
-void nn_forward_tc(const Launch& L, const NNGrid& g, const float* W, const float* R, float* D, int* err);
+void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const float* W, const float* R,
+                   float* D, int* err);
 
 }  // namespace pasm

@@ -29,14 +29,14 @@ constexpr int HW = TW + 2, HR = TR + 2;  // h tile: 16 x 16 (one 128-row MMA blo
 constexpr int AW = TW + 4, AR = TR + 4;  // a1 tile: 18 x 18
 constexpr int RW = TW + 6, RR = TR + 6;  // r tile: 20 x 20
 constexpr int PB = 8;                    // pairs per CTA
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;            // 8 warps: two per TMEM lane quarter
 
 constexpr int kPlane = AR * AW * PB * 16;          // bytes of one channel half of one branch
 constexpr int kA1Bytes = 4 * kPlane;               // 2 branches x 2 halves
 constexpr int kHBytes = HR * HW * PB * 16 * 4;     // float32 h (aliases the a1 space)
 constexpr int kRBytes = RR * RW * PB * 4;
 constexpr int kW2Bytes = 9 * 512;                  // bf16, canonical K-major, per tap 2x2 core matrices
-constexpr int kSmem = kA1Bytes + kRBytes + kW2Bytes + 2 * 144 * 4 + 16;
+constexpr int kSmem = kA1Bytes + kRBytes + kW2Bytes + 16;
 static_assert(kHBytes <= kA1Bytes, "h must fit in the a1 space");
 static_assert(HW * PB == 128, "one MMA block per h row");
 constexpr uint32_t kTmemCols = 512;                // 16 rows x 2 branches x 16 columns
@@ -74,17 +74,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Layers 1 and 3 (CUDA cores) read their weights from the kernel's parameter
+// space: every FMA takes its weight as a constant-bank operand, no load.
 __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, int k, int tiles_x,
-                                                       const float* __restrict__ W, const float* __restrict__ R,
-                                                       float* __restrict__ D, int* __restrict__ err) {
+                                                       const NNOuterWeights w13, const float* __restrict__ W,
+                                                       const float* __restrict__ R, float* __restrict__ D,
+                                                       int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* a1 = smem;                                           // [branch][half][AR][AW][PB][8] bf16
   float* hs = reinterpret_cast<float*>(smem);                   // [HR][HW][PB][16] f32 (after the MMAs)
   float* rs = reinterpret_cast<float*>(smem + kA1Bytes);        // [RR][RW][PB]
   uint8_t* w2 = smem + kA1Bytes + kRBytes;                      // 9 x [2 n-groups][2 k-chunks][8][8] bf16
-  float* w1 = reinterpret_cast<float*>(w2 + kW2Bytes);          // [9][16]
-  float* w3 = w1 + 144;                                         // [9][16]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(w3 + 144);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(w2 + kW2Bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -97,8 +98,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // weights: W1, W3 float32; W2 bf16 in the canonical layout (row n = output channel, k = input channel)
-  for (int t = tid; t < 144; t += kThreads) { w1[t] = W[t]; w3[t] = W[144 + 2304 + t]; }
+  // W2 as bf16 in the canonical layout (row n = output channel, k = input channel)
   for (int t = tid; t < 2304; t += kThreads) {
     const int tap = t / 256, ci = (t / 16) % 16, co = t % 16;   // W2[tap][ci][co]
     const int off = tap * 512 + (co % 8) * 16 + (co / 8) * 256 + (ci / 8) * 128 + (ci % 8) * 2;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
       for (int tap = 0; tap < 9; ++tap) {
         const float v = rs[((row + tap / 3) * RW + (col + tap % 3)) * PB + q];
 #pragma unroll
-        for (int o = 0; o < 16; ++o) z[o] = fmaf(w1[tap * 16 + o], v, z[o]);
+        for (int o = 0; o < 16; ++o) z[o] = fmaf(w13.w1[tap * 16 + o], v, z[o]);
       }
     }
     const int pix = (row * AW + col) * PB + q;  // 16-byte row index inside a plane
@@ -174,12 +174,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
   if (!done && tid == 0) atomicAdd(err, 1);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (done) {
-    // epilogue: TMEM lane m = 32 * warp + lane = (h pixel j, pair q) with m = j * PB + q
-    const int m = warp * 32 + lane;
+    // epilogue: TMEM lane m = 32 * (warp % 4) + lane = (h pixel j, pair q) with m = j * PB + q;
+    // the two warps of a lane quarter take alternate h rows
+    const int quarter = warp & 3, half = warp >> 2;
+    const int m = quarter * 32 + lane;
     const int j = m / PB, q = m % PB;
-    for (int i = 0; i < HR; ++i) {
+    for (int i = half; i < HR; i += 2) {
       float vp[16], vm[16];
-      const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16);
       tmem_ld16(lanebase + (uint32_t)((i * 2 + 0) * 16), vp);
       tmem_ld16(lanebase + (uint32_t)((i * 2 + 1) * 16), vm);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
@@ -209,9 +211,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
     float acc = 0.f;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const float* hp = hs + (((row + tap / 3) * HW + (col + tap % 3)) * PB + q) * 16;
+      const float4* hp = reinterpret_cast<const float4*>(hs + (((row + tap / 3) * HW + (col + tap % 3)) * PB + q) * 16);
 #pragma unroll
-      for (int ch = 0; ch < 16; ++ch) acc = fmaf(w3[tap * 16 + ch], hp[ch], acc);
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const float4 hv = hp[c4];
+        acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 0], hv.x, acc);
+        acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 1], hv.y, acc);
+        acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 2], hv.z, acc);
+        acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 3], hv.w, acc);
+      }
     }
     D[((int64_t)y * nx + x) * ldk + c] = c < k ? acc : 0.f;
   }
@@ -225,12 +233,13 @@ cudaError_t nn_tc_prepare() {
 
 bool nn_tc_supported(int ldk) { return ldk % PB == 0; }
 
-void nn_forward_tc(const Launch& L, const NNGrid& g, const float* W, const float* R, float* D, int* err) {
+void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const float* W, const float* R,
+                   float* D, int* err) {
   const int tiles_x = (g.nx + TW - 1) / TW, tiles_y = (g.ny + TR - 1) / TR;
   dim3 grid(tiles_x * tiles_y, g.ldk / PB);
   const double pix = (double)g.nx * g.ny * g.ldk;
   L.begin(KC_NN, pix * 8.0, pix * 2.0 * (2 * 9 * 16 + 2 * 9 * 256 + 9 * 16));
-  k_nn_tc<<<grid, kThreads, kSmem, L.s>>>(g.nx, g.ny, g.ldk, g.k, tiles_x, W, R, D, err);
+  k_nn_tc<<<grid, kThreads, kSmem, L.s>>>(g.nx, g.ny, g.ldk, g.k, tiles_x, w13, W, R, D, err);
   L.bump();
 }
 
