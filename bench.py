@@ -41,6 +41,9 @@ import meshgen as mg  # noqa: E402
 WORK = {"dim": 2, "N": 1024, "NH": 16, "k": 64, "tol": 1e-10, "target": 1e-9,
         "golden": "square_h1024_k72", "history": "square_h1024_H16_k64_history"}
 WORKLOAD_NAME = "unit-square P1 h=1/1024 (1046529 DoF), H=1/16 (225 DoF), 7 grids, k=64"
+# the 3D workload (a variant of the bench line): Kuhn P1 on the unit cube
+WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-10, "target": 1e-9,
+          "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history"}
 METRIC = "eigenpairs/s to 1e-9 rel. eigenvalue error"
 FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (measured 1.198)
 # kernel classes whose arithmetic is float64 in mixed mode (the V-cycle classes are float32 there)
@@ -148,16 +151,17 @@ def first_reach(hist, ref, target, ref_all=None):
     return out
 
 
-def reference_set():
+def reference_set(work=None):
     """the pairs the oracle's own iteration drives to 1e-9 on this workload
     (tests/golden history); None if the table is missing"""
-    p = os.path.join(ROOT, "tests", "golden", WORK["history"] + ".json")
+    w = WORK if work is None else work
+    p = os.path.join(ROOT, "tests", "golden", w["history"] + ".json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    ref_all = load_golden(WORK["golden"])
-    reach = first_reach(np.array(d["history"]), ref_all[:WORK["k"]], WORK["target"], ref_all)
+    ref_all = load_golden(w["golden"])
+    reach = first_reach(np.array(d["history"]), ref_all[:w["k"]], w["target"], ref_all)
     return np.where(reach >= 0)[0]
 
 
@@ -177,8 +181,9 @@ def time_to_target(reach, refset, cap):
 # ----------------------------------------------------------------------------- our arm
 
 def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, nn_weights=None, init=0,
-             smoother=None, nn_widths=None):
-    k = WORK["k"]
+             smoother=None, nn_widths=None, work=None):
+    w = WORK if work is None else work
+    k = w["k"]
     stream = torch.cuda.current_stream()
     A = [lv.A for lv in H.levels]
     M = [lv.M for lv in H.levels]
@@ -194,22 +199,22 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
     # intermediate levels; it is timed as the difference to a coarse start of the same context
     # the first pasm_init of a context runs the tile autotuner (kept for later inits): untimed
     t0 = time.perf_counter()
-    pg.pasm_init(ctx, k, WORK["tol"]); torch.cuda.synchronize()
+    pg.pasm_init(ctx, k, w["tol"]); torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
     init_ms = 0.0
     if init:
         torch.cuda.synchronize()
-        t0 = time.perf_counter(); pg.pasm_init(ctx, k, WORK["tol"]); torch.cuda.synchronize()
+        t0 = time.perf_counter(); pg.pasm_init(ctx, k, w["tol"]); torch.cuda.synchronize()
         t_nested = time.perf_counter() - t0
         ctx0 = pg.pasm_setup(A, M, H.P, pg.pasm_default_opts(precision=precision), stream.cuda_stream)
-        pg.pasm_init(ctx0, k, WORK["tol"]); torch.cuda.synchronize()
-        t0 = time.perf_counter(); pg.pasm_init(ctx0, k, WORK["tol"]); torch.cuda.synchronize()
+        pg.pasm_init(ctx0, k, w["tol"]); torch.cuda.synchronize()
+        t0 = time.perf_counter(); pg.pasm_init(ctx0, k, w["tol"]); torch.cuda.synchronize()
         t_coarse = time.perf_counter() - t0
         pg.pasm_destroy(ctx0)
         init_ms = max(0.0, (t_nested - t_coarse) * 1e3)
     # calibration (untimed): iterate from the start, record eigenvalues per step
-    pg.pasm_init(ctx, k, WORK["tol"])
+    pg.pasm_init(ctx, k, w["tol"])
     lam = np.zeros(k)
     hist = [None]
     pg.pasm_get(ctx, lam)
@@ -221,14 +226,14 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
         if act == 0:
             break
     hist = np.array(hist)
-    ref_all = load_golden(WORK["golden"])
-    reach = first_reach(hist, ref, WORK["target"], ref_all)
-    refset = reference_set()
+    ref_all = load_golden(w["golden"])
+    reach = first_reach(hist, ref, w["target"], ref_all)
+    refset = reference_set(w)
     conv, S = time_to_target(reach, refset, calib_steps)
     missed = [] if refset is None else [int(i) for i in refset if reach[i] < 0]
     launches = pg.pasm_last_launches(ctx)
     # timed: W warm-up steps then exactly K steps of the captured graph
-    pg.pasm_init(ctx, k, WORK["tol"])
+    pg.pasm_init(ctx, k, w["tol"])
     for _ in range(warmup):
         pg.pasm_step_async(ctx)
     torch.cuda.synchronize()
@@ -386,6 +391,13 @@ def main_ours(args):
     res["mixed_nested"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps, init=1)
     # the smoother of the paper's experiments (Section 5.1): 2 CG steps pre and post
     res["mixed_cg"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank, args.calib_steps, smoother=2)
+    # the 3D workload: Kuhn P1 on the cube, h = 1/128 (2,048,383 DoF), H = 1/8 (343), k = 32, mixed
+    if not args.no_3d:
+        H3 = mg.build_hierarchy(3, WORK3D["N"], WORK3D["NH"])
+        ref3 = load_golden(WORK3D["golden"])[:WORK3D["k"]]
+        res["cube_h128_H8_k32_mixed"] = run_mode(pg, torch, H3, ref3, 1, args.steps, args.warmup, rank,
+                                                 args.calib_steps, work=WORK3D)
+        del H3
     training = None
     if args.learned:
         w, train_s, losses = train_smoother(pg, torch, H)
@@ -543,6 +555,7 @@ def main():
     ap.add_argument("--learned", dest="learned", action="store_true", default=True,
                     help="also train the learned post-smoother and run the mixed mode with it (default)")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--no-3d", dest="no_3d", action="store_true", help="skip the 3D workload variant")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

@@ -49,6 +49,7 @@ HISTORIES = {
     # name: (dim, N_fine, N_coarse, k, tol, max_steps, nested start)
     "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40, False),
     "square_h1024_H16_k64_nested_history": (2, 1024, 16, 64, 1e-10, 40, True),
+    "cube_h128_H8_k32_history": (3, 128, 8, 32, 1e-10, 30, False),
 }
 
 
