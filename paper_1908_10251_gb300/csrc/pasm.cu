@@ -476,13 +476,21 @@ void free_k(pasm_ctx* c) {
   c->k = 0;
 }
 
+// The k-dependent buffers.  A re-initialisation with the same k keeps them and
+// the captured step graph (whose kernels take k and these pointers); only the
+// state below is cleared again.
 int alloc_k(pasm_ctx* c, int k) {
+  const bool reuse = !c->kallocs.empty() && c->k == k;
+  const size_t ldk = (size_t)ldk_for(k);
+  const size_t n = (size_t)c->lv.back().n;
+  const size_t nh = (size_t)c->NH * ldk;
+  const bool mixed = c->opts.precision == PASM_MIXED;
+  if (reuse) {
+    c->initialized = false;
+  } else {
   free_k(c);
   c->k = k;
-  c->ldk = ldk_for(k);
-  const size_t ldk = (size_t)c->ldk;
-  const size_t n = (size_t)c->lv.back().n;
-  const bool mixed = c->opts.precision == PASM_MIXED;
+  c->ldk = (int)ldk;
   auto& K = c->kallocs;
   AL(K, &c->U, n * ldk); AL(K, &c->Fd, n * ldk); AL(K, &c->X, n * ldk);
   AL(K, &c->YA, n * ldk); AL(K, &c->YM, n * ldk);
@@ -505,7 +513,6 @@ int alloc_k(pasm_ctx* c, int k) {
       else { double *p, *q; AL(K, &p, m); AL(K, &q, m); v.vP = p; v.vQ = q; }
     }
   }
-  const size_t nh = (size_t)c->NH * ldk;
   AL(K, &c->lam, ldk); AL(K, &c->lam2, ldk); AL(K, &c->alpha, ldk); AL(K, &c->bz, 2 * ldk);
   AL(K, &c->bq, nh); AL(K, &c->cq, nh); AL(K, &c->g, nh); AL(K, &c->uH, nh);
   AL(K, &c->partials, (size_t)c->max_border_blocks * 2 * ldk);
@@ -518,8 +525,12 @@ int alloc_k(pasm_ctx* c, int k) {
     AL(K, &c->cg.rr, ldk); AL(K, &c->cg.alpha, ldk); AL(K, &c->cg.beta, ldk);
   }
   if (c->proj_tc) {
-    const size_t words = proj_scratch_words(c->NH, 2 * ldk), tickets = proj_tickets(c->NH, 2 * ldk);
-    AL(K, &c->proj_hl, words); AL(K, &c->proj_tickets, tickets);
+    AL(K, &c->proj_hl, proj_scratch_words(c->NH, 2 * (int)ldk));
+    AL(K, &c->proj_tickets, proj_tickets(c->NH, 2 * (int)ldk));
+  }
+  }  // allocation
+  if (c->proj_tc) {
+    const size_t words = proj_scratch_words(c->NH, 2 * (int)ldk), tickets = proj_tickets(c->NH, 2 * (int)ldk);
     CK(cudaMemsetAsync(c->proj_hl, 0, sizeof(unsigned long long) * words, c->s));
     CK(cudaMemsetAsync(c->proj_tickets, 0, sizeof(unsigned int) * tickets, c->s));
   }
