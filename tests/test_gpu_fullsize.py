@@ -135,6 +135,36 @@ def test_fullsize_mixed_converges_to_reference(pg, square1024):
     pg.pasm_destroy(ctx)
 
 
+def test_fullsize_3d_fp64_steps_match_oracle_history(pg):
+    """The 3D workload at full size (Kuhn P1, h = 1/128, 2,048,383 DoF, H = 1/8,
+    k = 32), float64: six correction steps from the oracle's coarse initial
+    pairs against the oracle's own iterates (1e-10 relative) -- all 32 pairs
+    for the first three steps, afterwards the pairs the oracle drives to 1e-9
+    of the LOBPCG reference (of their own cluster), since the others iterate
+    chaotically as in 2D."""
+    with open(os.path.join(GOLDEN, "cube_h128_H8_k32_history.json")) as f:
+        hist = np.array(json.load(f)["history"])
+    ref_all = np.loadtxt(os.path.join(GOLDEN, "cube_h128_k40.txt"))
+    stable = np.array([cluster_err(row, ref_all) for row in hist]).min(axis=0) <= 1e-9
+    assert stable.sum() >= 4
+    H = mg.build_hierarchy(3, 128, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    k = 32
+    lam0, U0 = oracle.initial_state(prob, k)
+    assert np.allclose(lam0, hist[0], rtol=1e-12)
+    ctx = setup_ctx(pg, H, precision=0)
+    pg.pasm_init(ctx, k, 1e-10, lam0, U0)
+    lam = np.zeros(k)
+    for step in range(1, 7):
+        pg.pasm_step(ctx)
+        pg.pasm_get(ctx, lam)
+        rel = np.abs(lam - hist[step]) / hist[step]
+        if step > 3:
+            rel = rel[stable]
+        assert rel.max() < 1e-10, (step, int(rel.argmax()), rel.max())
+    pg.pasm_destroy(ctx)
+
+
 def test_fullsize_3d_mixed_converges_to_reference(pg):
     """The 3D workload at full size: Kuhn P1 on the unit cube, h = 1/128
     (2,048,383 DoF), H = 1/8 (343), k = 32, mixed precision.  The lowest four
