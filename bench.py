@@ -43,7 +43,8 @@ WORK = {"dim": 2, "N": 1024, "NH": 16, "k": 64, "tol": 1e-10, "target": 1e-9,
 WORKLOAD_NAME = "unit-square P1 h=1/1024 (1046529 DoF), H=1/16 (225 DoF), 7 grids, k=64"
 # the 3D workload (a variant of the bench line): Kuhn P1 on the unit cube
 WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-10, "target": 1e-9,
-          "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history"}
+          "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history",
+          "stable_history": "cube_h128_H8_k32_nofreeze_history"}
 METRIC = "eigenpairs/s to 1e-9 rel. eigenvalue error"
 FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (measured 1.198)
 # kernel classes whose arithmetic is float64 in mixed mode (the V-cycle classes are float32 there)
@@ -162,7 +163,16 @@ def reference_set(work=None):
         d = json.load(f)
     ref_all = load_golden(w["golden"])
     reach = first_reach(np.array(d["history"]), ref_all[:w["k"]], w["target"], ref_all)
-    return np.where(reach >= 0)[0]
+    out = np.where(reach >= 0)[0]
+    # where the oracle's run without freezing is available, keep only the pairs that are still
+    # within the target at its end (stable fixed points of the correction)
+    ps = os.path.join(ROOT, "tests", "golden", w.get("stable_history", "") + ".json")
+    if w.get("stable_history") and os.path.exists(ps):
+        with open(ps) as f:
+            last = np.array(json.load(f)["history"])[-1:]
+        ok = first_reach(last, ref_all[:w["k"]], w["target"], ref_all) >= 0
+        out = np.array([i for i in out if ok[i]], dtype=int)
+    return out
 
 
 def time_to_target(reach, refset, cap):

@@ -23,6 +23,7 @@ TABLES = {
     "square_h1024_k72": (2, 1024, 72, "shift-invert"),
     "square_h64_k16": (2, 64, 16, "shift-invert"),
     "cube_h128_k40": (3, 128, 40, "lobpcg"),
+    "square_h2048_k48": (2, 2048, 48, "lobpcg"),
 }
 
 
@@ -50,6 +51,8 @@ HISTORIES = {
     "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40, False),
     "square_h1024_H16_k64_nested_history": (2, 1024, 16, 64, 1e-10, 40, True),
     "cube_h128_H8_k32_history": (3, 128, 8, 32, 1e-10, 30, False),
+    # no freezing (tol 0): shows which converged pairs are stable fixed points of the correction
+    "cube_h128_H8_k32_nofreeze_history": (3, 128, 8, 32, 0.0, 40, False),
 }
 
 
