@@ -248,6 +248,7 @@ enum {
   PASM_KC_NN,           /* learned smoother (convolutions, training, fallback)    */
   PASM_KC_PROJ,         /* coarse projections Q^T b, Q^T c, Q g on tensor cores   */
   PASM_KC_CG,           /* conjugate-gradient smoothing (vectors and scalars)     */
+  PASM_KC_SWEEP_UPDATE, /* last Jacobi sweep fused with the outer update x += e    */
   PASM_KC_N
 };
 

@@ -256,7 +256,7 @@ def pasm_last_launches(ctx: Context) -> int:
     return n.value
 
 
-PASM_KC_N = 19
+PASM_KC_N = 20
 
 
 def pasm_trace_step(ctx: Context):

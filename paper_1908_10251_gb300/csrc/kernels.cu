@@ -6,6 +6,7 @@
 // the same matrices; Section 3.2 runs them independently).  A "row group" of
 // tpr threads owns one row, each thread CH chunks of one 16-byte vector.
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -675,6 +676,81 @@ void cast_d2f(const Launch& L, const double* in, float* out, int64_t count) {
 }  // namespace pasm
 
 namespace pasm {
+
+// ----------------------------------------------------------------------------------------------
+// The last Jacobi sweep of the top-level V-cycle fused with the outer update of
+// the mixed path: e' = z + omega dinv (y - A z) in float32 as k_rowop<float, JACOBI>,
+// then X = B + e' in double-float ((hi, lo) float pairs, B in pairs or float64),
+// so e' is never stored.
+template <int CH, bool BFF>
+__global__ void __launch_bounds__(kBlock)
+    k_jacobi_axpy_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float* __restrict__ av,
+                     const float* __restrict__ E, const float* __restrict__ F, const float* __restrict__ dinv,
+                     float omega, const double* B, double* X, int ldk, int tpr) {
+  constexpr int V = 4;
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  float acc[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[c][v] = 0.f;
+  const size_t base = (size_t)row * ldk;
+  float y[CH][V], z[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    Vec16<float>::load(F + base + (c * tpr + lane) * V, y[c]);
+    Vec16<float>::load(E + base + (c * tpr + lane) * V, z[c]);
+  }
+  const float w = omega * dinv[row];
+  gather_rows<float, CH>(ci, av, nullptr, 0.f, E, rp[row], rp[row + 1], lane, tpr, ldk, acc);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const size_t off = base + (c * tpr + lane) * V;
+    float h[V], l[V];
+    if (BFF) {
+      const float4 b0 = *reinterpret_cast<const float4*>(B + off);
+      const float4 b1 = *reinterpret_cast<const float4*>(B + off + 2);
+      h[0] = b0.x; l[0] = b0.y; h[1] = b0.z; l[1] = b0.w; h[2] = b1.x; l[2] = b1.y; h[3] = b1.z; l[3] = b1.w;
+    } else {
+      const double2 b0 = *reinterpret_cast<const double2*>(B + off);
+      const double2 b1 = *reinterpret_cast<const double2*>(B + off + 2);
+      ff_split(b0.x, h[0], l[0]); ff_split(b0.y, h[1], l[1]); ff_split(b1.x, h[2], l[2]); ff_split(b1.y, h[3], l[3]);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float e = fmaf(w, y[c][v] - acc[c][v], z[c][v]);
+      ff_mac(h[v], l[v], e, 0.f, 1.f, 0.f);
+      ff_norm(h[v], l[v]);
+    }
+    *reinterpret_cast<float4*>(X + off) = make_float4(h[0], l[0], h[1], l[1]);
+    *reinterpret_cast<float4*>(X + off + 2) = make_float4(h[2], l[2], h[3], l[3]);
+  }
+}
+
+void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float* F, const float* dinv, float omega,
+                    const double* B, bool b_ff, double* X, int ldk) {
+  if (A.n_rows == 0) return;
+  const Geo g = geometry<float>(ldk, L.geo);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double rows = A.n_rows, cols = A.n_cols, nnz = (double)A.nnz;
+    L.rows(A.n_rows);
+    L.begin(KC_SWEEP_UPDATE, nnz * 8.0 + (rows + 1) * 4.0 + cols * ldk * 4.0 + rows * ldk * (4.0 + 16.0) + rows * 4.0,
+            2.0 * nnz * ldk + 4.0 * rows * ldk);
+  }
+  if (b_ff) {
+    PASM_DISPATCH_CH(g.ch, k_jacobi_axpy_ff<CH, true><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v32, E, F, dinv,
+                                                                                 omega, B, X, ldk, g.tpr));
+  } else {
+    PASM_DISPATCH_CH(g.ch, k_jacobi_axpy_ff<CH, false><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v32, E, F,
+                                                                                  dinv, omega, B, X, ldk, g.tpr));
+  }
+  L.bump();
+}
 
 // ----------------------------------------------------------------------------------------------
 // Conjugate-gradient smoother (the multigrid smoother of the paper's experiments, Section 5.1):

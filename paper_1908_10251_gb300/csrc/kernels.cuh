@@ -25,7 +25,7 @@ template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
 // Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
 enum KernelClass {
   KC_JACOBI = 0, KC_JACOBI0, KC_RESID, KC_SPMM, KC_PROLONG, KC_DENSE, KC_OUTER_RHS, KC_OUTER_RES, KC_AXPY,
-  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_PROJ, KC_CG, KC_N
+  KC_BORDER, KC_COLSUM, KC_INIT, KC_SECULAR, KC_UPDATE, KC_COUNT, KC_CAST, KC_NN, KC_PROJ, KC_CG, KC_SWEEP_UPDATE, KC_N
 };
 
 // Host-side event recorder (defined in pasm.cu); null when not tracing.
@@ -157,6 +157,10 @@ void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const d
 // YA = A X, YM = M X (X, YA, YM in pairs) and float64 partial sums as border_products.
 int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* X, double* YA, double* YM,
                        double* partials, int ldk, int max_blocks);
+// Last float32 Jacobi sweep of the top-level V-cycle fused with X = B + e'
+// (e' = E + omega dinv .* (F - A E), never stored; X in pairs, B in pairs if b_ff).
+void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float* F, const float* dinv, float omega,
+                    const double* B, bool b_ff, double* X, int ldk);
 // out = S X; x_ff / out_ff: X / out in pairs (else float64).
 void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk);
 // X = B + E (X in pairs; B in pairs if b_ff, else float64; X may alias B).

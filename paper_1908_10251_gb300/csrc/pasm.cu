@@ -287,8 +287,16 @@ int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
   return 1;
 }
 
+// Top-level output of a mixed-precision V-cycle: the last post-smoothing sweep
+// writes X = B + e directly (double-float pairs) instead of e.
+struct TopOut {
+  const double* B;
+  bool b_ff;
+  double* X;
+};
+
 template <typename T>
-T* vcycle(pasm_ctx* c, int l) {
+T* vcycle(pasm_ctx* c, int l, const TopOut* top = nullptr) {
   const Launch L = launcher(c);
   LevelDev& v = c->lv[l];
   T* F = (T*)v.vF;
@@ -341,6 +349,12 @@ T* vcycle(pasm_ctx* c, int l) {
   if (Fused<T>::on) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
   if (s == 1) std::swap(cur, tmp);
   for (; s < c->opts.nu_post; ++s) {
+    if (Fused<T>::on && top && s == c->opts.nu_post - 1) {
+      // last sweep fused with the outer update; the cycle's result is in top->X
+      jacobi_axpy_ff(launcher(c, l, PASM_TILE_JACOBI), v.A, (const float*)cur, (const float*)F, v.dinv32, (float)om,
+                     top->B, top->b_ff, top->X, ldk);
+      return nullptr;
+    }
     rowop<T>(launcher(c, l, PASM_TILE_JACOBI), OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
@@ -358,12 +372,14 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
     // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
     to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
     outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
-    T* e = vcycle<T>(c, lt);
-    axpy_ff(L, v.n, U, false, (const float*)e, X, c->ldk);
+    const TopOut first{U, false, X};
+    T* e = vcycle<T>(c, lt, lt >= 1 ? &first : nullptr);
+    if (e) axpy_ff(L, v.n, U, false, (const float*)e, X, c->ldk);
     for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
       outer_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RES), v.A, c->Fd, X, (float*)Ftop, c->ldk);
-      e = vcycle<T>(c, lt);
-      axpy_ff(L, v.n, X, true, (const float*)e, X, c->ldk);
+      const TopOut next{X, true, X};
+      e = vcycle<T>(c, lt, lt >= 1 ? &next : nullptr);
+      if (e) axpy_ff(L, v.n, X, true, (const float*)e, X, c->ldk);
     }
     return;
   }
@@ -1371,7 +1387,7 @@ int pasm_trace_launches(pasm_ctx* c, int max, int* cls, int* rows, float* ms, do
 const char* pasm_kernel_class_name(int cls) {
   static const char* names[KC_N] = {"jacobi", "jacobi0", "resid", "spmm", "prolong", "dense", "outer_rhs",
                                     "outer_res", "axpy", "border", "colsum", "init", "secular", "update",
-                                    "count", "cast", "nn", "proj", "cg"};
+                                    "count", "cast", "nn", "proj", "cg", "sweep_update"};
   return (cls >= 0 && cls < KC_N) ? names[cls] : "unknown";
 }
 
