@@ -286,7 +286,8 @@ template <int CH, bool WFF>
 __global__ void __launch_bounds__(kBlock)
     k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
                 const double* __restrict__ W, const double* __restrict__ X, const double* __restrict__ alpha,
-                const int* __restrict__ upd, double* __restrict__ U, int ldk, int tpr, int identity) {
+                const int* __restrict__ upd, double* __restrict__ U, double* __restrict__ Usplit, int ldk, int tpr,
+                int identity) {
   const int rpb = kBlock / tpr;
   const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
@@ -318,6 +319,12 @@ __global__ void __launch_bounds__(kBlock)
     if (upd[col]) u.x = r[0];
     if (upd[col + 1]) u.y = r[1];
     *reinterpret_cast<double2*>(U + off) = u;
+    if (Usplit) {  // the (hi, lo) copy of U the next step's gathers read
+      float uh[2], ul[2];
+      ff_split(u.x, uh[0], ul[0]);
+      ff_split(u.y, uh[1], ul[1]);
+      store_pair<true>(Usplit, off, uh, ul);
+    }
   }
 }
 
@@ -417,7 +424,7 @@ void from_ff(const Launch& L, int64_t total, const double* in, double* out) {
 }
 
 void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
-                     const double* alpha, const int* upd, double* U, int ldk) {
+                     const double* alpha, const int* upd, double* U, double* Usplit, int ldk) {
   const Geo g = geometry_ff(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
   const int grid = (n + rpb - 1) / rpb;
@@ -431,11 +438,11 @@ void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, boo
   const int* ci = P ? P->ci : nullptr;
   const float2* pv = P ? P->vff : nullptr;
   if (w_ff) {
-    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, true><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, ldk,
-                                                                            g.tpr, identity));
+    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, true><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, Usplit,
+                                                                            ldk, g.tpr, identity));
   } else {
-    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, false><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, ldk,
-                                                                             g.tpr, identity));
+    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, false><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, Usplit,
+                                                                             ldk, g.tpr, identity));
   }
   L.bump();
 }

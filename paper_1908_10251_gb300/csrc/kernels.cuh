@@ -169,9 +169,10 @@ void axpy_ff(const Launch& L, int n, const double* B, bool b_ff, const float* E,
 void to_ff(const Launch& L, int64_t total, const double* in, double* out);
 void from_ff(const Launch& L, int64_t total, const double* in, double* out);
 // U = alpha X + P W for updated pairs (float64 U, X in pairs, W in pairs if
-// w_ff); P == nullptr means P = identity on n rows.
+// w_ff); P == nullptr means P = identity on n rows.  Usplit (optional)
+// receives U as pairs.
 void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
-                     const double* alpha, const int* upd, double* U, int ldk);
+                     const double* alpha, const int* upd, double* U, double* Usplit, int ldk);
 
 // ----------------------------------------------------------------------------------------------
 // Float64-accurate dense product C = A B on the tensor cores (proj_tc.cu).

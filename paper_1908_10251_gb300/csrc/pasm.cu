@@ -364,13 +364,13 @@ T* vcycle(pasm_ctx* c, int l, const TopOut* top = nullptr) {
 // Algorithm 1 step 1 on level lt: X = result of the V-cycles for A x = lam M U from x = U,
 // each cycle a defect correction x += V(f - A x) with f = lam M U (float64 residual).
 template <typename T>
-void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X) {
+void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X, bool u_split) {
   const Launch L = launcher(c);
   LevelDev& v = c->lv[lt];
   T* Ftop = (T*)v.vF;
   if (Fused<T>::on) {
     // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
-    to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
+    if (!u_split) to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
     outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
     const TopOut first{U, false, X};
     T* e = vcycle<T>(c, lt, lt >= 1 ? &first : nullptr);
@@ -393,9 +393,11 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
   }
 }
 
-void bvp(pasm_ctx* c, int lt, const double* lam, const double* U, double* X) {
-  if (c->opts.precision == PASM_MIXED) bvp_impl<float>(c, lt, lam, U, X);
-  else bvp_impl<double>(c, lt, lam, U, X);
+// u_split: c->Uff already holds U in pairs (the state U of a step: the update of
+// the previous step, or pasm_init, wrote it); otherwise it is formed here.
+void bvp(pasm_ctx* c, int lt, const double* lam, const double* U, double* X, bool u_split = false) {
+  if (c->opts.precision == PASM_MIXED) bvp_impl<float>(c, lt, lam, U, X, u_split);
+  else bvp_impl<double>(c, lt, lam, U, X, u_split);
 }
 
 struct PairState {
@@ -468,7 +470,9 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
     w_ff = ff;
   }
   const Launch Lu = launcher(c, lt, PASM_TILE_UPDATE);
-  if (ff) update_pairs_ff(Lu, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, ldk);
+  // the finest-level state update also refreshes the pair copy of U for the next step
+  double* usplit = (ff && ps.Uout == c->U && lt == c->nlev - 1) ? c->Uff : nullptr;
+  if (ff) update_pairs_ff(Lu, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, usplit, ldk);
   else if (lt >= 1) update_pairs(Lu, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
   else update_pairs_identity(Lu, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
 }
@@ -476,7 +480,7 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
 // One correction step for all active pairs on the finest level.
 void step_body(pasm_ctx* c) {
   const int lt = c->nlev - 1;
-  bvp(c, lt, c->lam, c->U, c->X);
+  bvp(c, lt, c->lam, c->U, c->X, true);
   PairState ps{c->lam, c->active, c->steps, c->status, c->U, c->tol};
   augmented(c, lt, c->X, ps);
   count_active(launcher(c), c->active, c->k, c->nact);
@@ -888,7 +892,7 @@ static int autotune(pasm_ctx* c) {
         pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); });
       const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
       pick(l, PASM_TILE_UPDATE, c64, [&](const Launch& L) {
-        update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->U, ldk);
+        update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->U, nullptr, ldk);
       });
     } else {
       double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
@@ -982,6 +986,8 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
     if (r) return r;
     CK(cudaMemsetAsync(c->nn.accepted, 0, sizeof(int) * 256, c->s));
   }
+  // the pair copy of the state U that the first step's gathers read (later steps: the update)
+  if (c->opts.precision == PASM_MIXED) to_ff(L, (int64_t)nf * c->ldk, c->U, c->Uff);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
   c->initialized = true;
@@ -1067,6 +1073,7 @@ int pasm_bvp(pasm_ctx* c, const double* lambda, const double* U, double* Uhat) {
   if (c->opts.precision == PASM_MIXED) {  // u~ comes back in (hi, lo) pairs
     from_ff(launcher(c), (int64_t)nf * c->ldk, c->X, c->YA);
     xout = c->YA;
+    to_ff(launcher(c), (int64_t)nf * c->ldk, c->U, c->Uff);  // the step's pair copy of the state U again
   }
   r = get_block(c, xout, Uhat, nf);
   if (r) return r;
