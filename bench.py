@@ -175,6 +175,26 @@ def reference_set(work=None):
     return out
 
 
+def max_over_ranks(torch, x):
+    """The maximum of a float over all ranks, then a barrier (the job's time is
+    its slowest replica's); the value itself on a single process.  CUDA tensors
+    with NCCL, CPU tensors with gloo."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return x
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.barrier()
+    return float(t.item())
+
+
+def job_value(world, converged, steps_to_target, ms_step, start_ms=0.0):
+    """Whole-job throughput of N replicas: every rank converges `converged`
+    pairs in steps_to_target steps of ms_step (the max over ranks) plus an
+    optional start cost, so the job delivers world * converged pairs in that time."""
+    return world * converged / ((steps_to_target * ms_step + start_ms) / 1e3)
+
+
 def time_to_target(reach, refset, cap):
     """(pairs counted, steps S): over the reference set when known -- every set
     pair must reach the target, a missing one costs the whole step cap -- else
@@ -258,12 +278,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
             pg.pasm_step_async(ctx)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    if torch.distributed.is_initialized():
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-        torch.distributed.barrier()
+    ms = max_over_ranks(torch, e0.elapsed_time(e1))
     ms_step = ms / steps
     # per-kernel-class event timing of a few eager steps (same arithmetic)
     trace = {}
@@ -428,7 +443,7 @@ def main_ours(args):
     primary, primary_prec = modes[0]
     main = res[primary]
     S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
-    value = world * conv / (S * ms_step / 1e3)
+    value = job_value(world, conv, S, ms_step)
     if args.no_e2e:
         e2e_s, bin_, bout, e2e_value = None, 0, 0, None
     else:
@@ -530,7 +545,7 @@ def main_ours(args):
         "gpu_launches": int(args.steps * main["launches_per_step"]),
         "clocks": main["clocks"],
         "kernels": classes,
-        "variants": {name: {"value": world * r["converged"] / ((r["S"] * r["ms_per_step"] + r["init_ms"]) / 1e3),
+        "variants": {name: {"value": job_value(world, r["converged"], r["S"], r["ms_per_step"], r["init_ms"]),
                             "ms_per_step": r["ms_per_step"], "steps_to_1e-9": r["S"], "init_ms": r["init_ms"],
                             "pairs_converged": r["converged"], "missed": r["missed"], "clocks": r["clocks"],
                             "learned_steps_accepted": r["accepted"]}

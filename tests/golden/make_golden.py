@@ -31,7 +31,8 @@ def write(name):
     dim, N, count, method = TABLES[name]
     t = time.time()
     if method == "lobpcg":
-        vals, res = smallest_eigenvalues_lobpcg(mg.build_hierarchy(dim, N, 8), count, tol=1e-9)
+        Nc = 8 if dim == 3 else 16     # a coarse space large enough to seed count + 8 vectors
+        vals, res = smallest_eigenvalues_lobpcg(mg.build_hierarchy(dim, N, Nc), count, tol=1e-9)
         how = "LOBPCG, multigrid preconditioner, max relative residual %.1e" % res
     else:
         A, M = mg.assemble(dim, N)
