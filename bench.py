@@ -45,6 +45,10 @@ WORKLOAD_NAME = "unit-square P1 h=1/1024 (1046529 DoF), H=1/16 (225 DoF), 7 grid
 WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-10, "target": 1e-9,
           "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history",
           "stable_history": "cube_h128_H8_k32_nofreeze_history"}
+# the h = 1/2048 workload (4,190,209 DoF, H = 1/16, 8 grids, k = 128): its reference table holds the
+# 48 smallest eigenvalues, so only pairs 0..47 can be counted; no oracle history at this size
+WORK5 = {"dim": 2, "N": 2048, "NH": 16, "k": 128, "tol": 1e-10, "target": 1e-9,
+         "golden": "square_h2048_k48", "history": None}
 METRIC = "eigenpairs/s to 1e-9 rel. eigenvalue error"
 FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (measured 1.198)
 # kernel classes whose arithmetic is float64 in mixed mode (the V-cycle classes are float32 there)
@@ -143,7 +147,7 @@ def first_reach(hist, ref, target, ref_all=None):
     ref_all = ref if ref_all is None else ref_all
     cid = clusters(ref_all)
     out = np.full(hist.shape[1], -1)
-    for i in range(hist.shape[1]):
+    for i in range(min(hist.shape[1], len(ref_all))):
         members = ref_all[cid == cid[i]]
         err = np.min(np.abs(hist[:, i][:, None] - members[None, :]) / members[None, :], axis=1)
         ok = np.where(err <= target)[0]
@@ -156,6 +160,8 @@ def reference_set(work=None):
     """the pairs the oracle's own iteration drives to 1e-9 on this workload
     (tests/golden history); None if the table is missing"""
     w = WORK if work is None else work
+    if not w.get("history"):
+        return None
     p = os.path.join(ROOT, "tests", "golden", w["history"] + ".json")
     if not os.path.exists(p):
         return None
@@ -429,6 +435,13 @@ def main_ours(args):
         res["cube_h128_H8_k32_mixed"] = run_mode(pg, torch, H3, ref3, 1, args.steps, args.warmup, rank,
                                                  args.calib_steps, work=WORK3D)
         del H3
+    # the h = 1/2048, k = 128 workload (when its reference table is present)
+    H5 = None
+    if not args.no_c5 and os.path.exists(os.path.join(ROOT, "tests", "golden", WORK5["golden"] + ".txt")):
+        H5 = mg.build_hierarchy(WORK5["dim"], WORK5["N"], WORK5["NH"])
+        ref5 = load_golden(WORK5["golden"])
+        res["square_h2048_H16_k128_mixed"] = run_mode(pg, torch, H5, ref5, 1, args.steps, args.warmup, rank,
+                                                      args.calib_steps, work=WORK5)
     training = None
     if args.learned:
         w, train_s, losses = train_smoother(pg, torch, H)
@@ -439,7 +452,15 @@ def main_ours(args):
         coarse[-2:] = 0
         res["mixed_learned_coarse"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank,
                                                args.calib_steps, nn_weights=w, nn_widths=coarse)
+        if H5 is not None:
+            # the same network (the 2D stencil is h-independent) on the h = 1/2048 workload
+            coarse5 = grid_widths(H5)
+            coarse5[-2:] = 0
+            res["square_h2048_H16_k128_learned_coarse"] = run_mode(
+                pg, torch, H5, load_golden(WORK5["golden"]), 1, args.steps, args.warmup, rank, args.calib_steps,
+                nn_weights=w, nn_widths=coarse5, work=WORK5)
         training = {"seconds": train_s, "loss_first": losses[0], "loss_last": losses[-1]}
+    H5 = None
     primary, primary_prec = modes[0]
     main = res[primary]
     S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
@@ -600,6 +621,7 @@ def main():
                     help="also train the learned post-smoother and run the mixed mode with it (default)")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-3d", dest="no_3d", action="store_true", help="skip the 3D workload variant")
+    ap.add_argument("--no-c5", dest="no_c5", action="store_true", help="skip the h = 1/2048, k = 128 variant")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

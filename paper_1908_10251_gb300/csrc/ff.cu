@@ -281,7 +281,8 @@ __global__ void k_from_ff(int64_t total, const double* __restrict__ in, double* 
 }
 
 // U[row][c] = upd[c] ? alpha[c] X[row][c] + (P W)[row][c] : U[row][c], X as
-// float pairs, W as float pairs (WFF) or float64; identity: P W = W.
+// float pairs, W as float pairs (WFF) or float64; identity: P W = W.  Entries
+// of frozen pairs are neither read nor written.
 template <int CH, bool WFF>
 __global__ void __launch_bounds__(kBlock)
     k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
@@ -304,9 +305,12 @@ __global__ void __launch_bounds__(kBlock)
   for (int c = 0; c < CH; ++c) {
     const int col = (c * tpr + lane) * 2;
     const size_t off = base + col;
+    const int u0 = upd[col], u1 = upd[col + 1];
+    if (!u0 && !u1) continue;  // both pairs frozen: U and its split copy stay as they are
     float xh[2], xl[2];
     load_pair<true>(X, off, xh, xl);
-    double2 u = *reinterpret_cast<const double2*>(U + off);
+    double2 u;
+    if (!(u0 && u1)) u = *reinterpret_cast<const double2*>(U + off);
     double r[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
@@ -316,8 +320,8 @@ __global__ void __launch_bounds__(kBlock)
       ff_mac(h, l, ah, al, xh[v], xl[v]);
       r[v] = ff_to_double(h, l);
     }
-    if (upd[col]) u.x = r[0];
-    if (upd[col + 1]) u.y = r[1];
+    if (u0) u.x = r[0];
+    if (u1) u.y = r[1];
     *reinterpret_cast<double2*>(U + off) = u;
     if (Usplit) {  // the (hi, lo) copy of U the next step's gathers read
       float uh[2], ul[2];

@@ -214,7 +214,7 @@ template <typename T, int CH>
 __global__ void __launch_bounds__(kBlock) k_jacobi2_zero(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                           const T* __restrict__ av, const T* __restrict__ dinv,
                                                           T omega, const T* __restrict__ F, T* __restrict__ out,
-                                                          int ldk, int tpr) {
+                                                          int ldk, int tpr, int prescaled) {
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
   const int row = blockIdx.x * rpb + threadIdx.x / tpr;
@@ -230,7 +230,8 @@ __global__ void __launch_bounds__(kBlock) k_jacobi2_zero(int n, const int* __res
   T f[CH][V];
 #pragma unroll
   for (int c = 0; c < CH; ++c) ldg16<T>(F + base + (c * tpr + lane) * V, f[c]);
-  gather_rows<T, CH>(ci, av, dinv, omega, F, rp[row], rp[row + 1], lane, tpr, ldk, acc);
+  // prescaled: av already holds omega a_ij / a_jj
+  gather_rows<T, CH>(ci, av, prescaled ? nullptr : dinv, omega, F, rp[row], rp[row + 1], lane, tpr, ldk, acc);
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const size_t off = base + (c * tpr + lane) * V;
@@ -294,8 +295,10 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
     L.begin(KC_JACOBI, nnz * (4.0 + sz) + (rows + 1) * 4.0 + rows * sz + 2.0 * rows * ldk * sz,
             3.0 * nnz * ldk + 2.0 * rows * ldk);
   }
-  PASM_DISPATCH_CH(g.ch, k_jacobi2_zero<T, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, vals<T>(A), dinv,
-                                                                          omega, F, out, ldk, g.tpr));
+  const T* ws = scaled_vals<T>(A);
+  PASM_DISPATCH_CH(g.ch, k_jacobi2_zero<T, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, ws ? ws : vals<T>(A),
+                                                                          dinv, omega, F, out, ldk, g.tpr,
+                                                                          ws ? 1 : 0));
   L.bump();
 }
 

@@ -16,11 +16,17 @@ struct DCsr {
   double* v64 = nullptr;
   float* v32 = nullptr;
   float2* vff = nullptr;  // (hi, lo) float split of v64 for the double-float kernels (mixed precision)
+  // omega a_ij / a_jj (A only): the values of the second Jacobi sweep from a zero start
+  double* w64 = nullptr;
+  float* w32 = nullptr;
 };
 
 template <typename T> inline const T* vals(const DCsr& m);
 template <> inline const double* vals<double>(const DCsr& m) { return m.v64; }
 template <> inline const float* vals<float>(const DCsr& m) { return m.v32; }
+template <typename T> inline const T* scaled_vals(const DCsr& m);
+template <> inline const double* scaled_vals<double>(const DCsr& m) { return m.w64; }
+template <> inline const float* scaled_vals<float>(const DCsr& m) { return m.w32; }
 
 // Kernel classes for tracing (keep in sync with PASM_KC_* in pasm.h).
 enum KernelClass {

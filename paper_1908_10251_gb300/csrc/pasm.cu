@@ -691,6 +691,17 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
       AL(c->allocs, &v.dinv32, (size_t)v.n);
       CK(cudaMemcpy(v.dinv32, df.data(), sizeof(float) * v.n, cudaMemcpyHostToDevice));
     }
+    // omega a_ij / a_jj: the second Jacobi sweep from a zero start gathers f with these values
+    // (x1 = omega D^-1 f, so A x1 = (omega A D^-1) f), with no per-entry load of a_jj (the fused
+    // two-sweep kernel runs in the float32 cycles of mixed precision)
+    if (mixed) {
+      const int64_t nnz = A[l].row_ptr[v.n];
+      std::vector<double> w((size_t)nnz);
+      for (int64_t q = 0; q < nnz; ++q) w[(size_t)q] = c->opts.omega * A[l].val[q] * di[(size_t)A[l].col[q]];
+      std::vector<float> wf(w.begin(), w.end());
+      AL(c->allocs, &v.A.w32, (size_t)nnz);
+      CK(cudaMemcpy(v.A.w32, wf.data(), sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice));
+    }
     if (l >= 1) {
       const pasm_csr& p = P[l - 1];
       r = upload_csr(c, p, v.P, mixed, mixed);
@@ -810,8 +821,9 @@ extern "C++" {
 // valid number of 16-byte chunks per thread (1, 2, 4, 8) on the level's own
 // matrices (one warm-up, then the mean of three launches, CUDA events on the
 // context's stream) and keep the fastest.  Runs once per block width ldk; the
-// buffers it uses are scratch of the step (the update runs with no pair
-// selected, so U is read and rewritten unchanged).
+// buffers it uses are scratch of the step (the mixed-precision update writes
+// into scratch; the float64 update runs with no pair selected, so U is read
+// and rewritten unchanged).
 static constexpr int kTuneRows = 16384;
 
 template <typename Fn>
@@ -891,9 +903,13 @@ static int autotune(pasm_ctx* c) {
       if (l < c->nlev - 1)
         pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); });
       const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
+      // the update skips frozen pairs, so it is timed with every pair selected, writing
+      // into scratch (YM) instead of U
+      CK(cudaMemsetAsync(c->upd, 1, sizeof(int) * (size_t)ldk, c->s));
       pick(l, PASM_TILE_UPDATE, c64, [&](const Launch& L) {
-        update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->U, nullptr, ldk);
+        update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->YM, nullptr, ldk);
       });
+      CK(cudaMemsetAsync(c->upd, 0, sizeof(int) * (size_t)ldk, c->s));
     } else {
       double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
       const double om = c->opts.omega;

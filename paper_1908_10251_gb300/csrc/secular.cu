@@ -35,6 +35,7 @@
 #include "kernels.cuh"
 
 #include <cfloat>
+#include <climits>
 
 namespace pasm {
 
@@ -141,6 +142,7 @@ __device__ __forceinline__ void sums32(const float (&dd)[kPer], const float (&zz
   psi = dpsi = phi = dphi = 0.f;
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
+    if (32 * q >= nJ) break;  // warp-uniform: skip the unused register slots
     const int t = lane + 32 * q;
     if (t < nJ) {
       float del = dd[q] - tau;
@@ -272,11 +274,71 @@ __device__ __forceinline__ void root_vector_sums(const SecShared& S, int nK, int
   ny2 = warp_sum(ny2); yc = warp_sum(yc);
 }
 
+// A selection candidate: score, Ritz value, preference order, kind (0 root,
+// 1 deflated pole, 2 merged-away pole) and index.  No candidate yet: sc = -1
+// (scores are >= 0; NaN scores are never taken).
+struct Cand {
+  double sc, th;
+  int ord, kind, idx;
+  __device__ void clear() { sc = -1.0; th = 0.0; ord = INT_MAX; kind = 0; idx = -1; }
+  __device__ bool beats(const Cand& o) const {
+    return sc > o.sc || (sc == o.sc && (th < o.th || (th == o.th && ord < o.ord)));
+  }
+  __device__ void offer(double s2, double t2, int o2, int k2, int i2) {
+    Cand c;
+    c.sc = s2; c.th = t2; c.ord = o2; c.kind = k2; c.idx = i2;
+    if (c.beats(*this)) *this = c;
+  }
+};
+
+__device__ __forceinline__ Cand shfl_cand(const Cand& c, int o) {
+  Cand r;
+  r.sc = __shfl_xor_sync(0xffffffffu, c.sc, o);
+  r.th = __shfl_xor_sync(0xffffffffu, c.th, o);
+  r.ord = __shfl_xor_sync(0xffffffffu, c.ord, o);
+  r.kind = __shfl_xor_sync(0xffffffffu, c.kind, o);
+  r.idx = __shfl_xor_sync(0xffffffffu, c.idx, o);
+  return r;
+}
+
+// The best candidate of the block (every thread gets it).
+__device__ __forceinline__ Cand block_best(Cand c, Cand* buf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const Cand t = shfl_cand(c, o);
+    if (t.beats(c)) c = t;
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) buf[w] = c;
+  __syncthreads();
+  Cand r = buf[0];
+  for (int q = 1; q < kSecWarps; ++q)
+    if (buf[q].beats(r)) r = buf[q];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int block_min(int v, int* buf) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) buf[w] = v;
+  __syncthreads();
+  int r = buf[0];
+  for (int q = 1; q < kSecWarps; ++q) r = min(r, buf[q]);
+  __syncthreads();
+  return r;
+}
+
 __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   extern __shared__ double smem[];
   __shared__ double red[32];
   __shared__ int s_nJ, s_nK, s_m0, s_best, s_best_defl, s_cert, s_list[64], s_nlist;
   __shared__ double s_lower, s_upper;
+  __shared__ Cand s_cand[kSecWarps];
+  __shared__ int s_imin[kSecWarps];
   const int i = blockIdx.x;
   const int NH = a.NH, ldk = a.ldk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -407,19 +469,23 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     if (phase > 0)
       for (int m = tid; m <= mmax; m += kSecThreads) S.solved[m] = 1;
     __syncthreads();
-    if (tid == 0) {
-      // best candidate among solved roots and deflated poles
-      double best = -1.0, best_th = 0.0, mass = 0.0;
-      int bi = -1, bdefl = 0, nsolved = 0, m_unsolved = -1;
-      for (int m = 0; m <= nJ; ++m) {
-        if (!S.solved[m]) { if (m_unsolved < 0) m_unsolved = m; continue; }
+    {
+      // best candidate among solved roots and deflated poles: each thread scans
+      // its share, then a block reduction.  Order of preference: larger score,
+      // then smaller theta, then roots before deflated poles, lower index first.
+      Cand best;
+      best.clear();
+      double mass = 0.0;
+      int nsolved = 0, m_unsolved = INT_MAX;
+      for (int m = tid; m <= nJ; m += kSecThreads) {
+        if (!S.solved[m]) { m_unsolved = min(m_unsolved, m); continue; }
         ++nsolved;
         const double sbm = S.sb[m];
         mass += sbm * sbm;
         const double sc = a.score_norm == 0 ? fabs(sbm) / sqrt(S.theta[m]) : fabs(sbm);
-        if (sc > best || (sc == best && S.theta[m] < best_th)) { best = sc; best_th = S.theta[m]; bi = m; bdefl = 0; }
+        best.offer(sc, S.theta[m], m, 0, m);
       }
-      for (int j = 0; j < NH; ++j) {
+      for (int j = tid; j < NH; j += kSecThreads) {
         double sbj, thj;
         int kind;
         if (!(fabs(S.z[j]) > tolz)) {            // plain deflation: eigenvector e_j
@@ -433,25 +499,31 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
         }
         mass += sbj * sbj;
         const double sc = a.score_norm == 0 ? fabs(sbj) / sqrt(thj) : fabs(sbj);
-        if (sc > best || (sc == best && thj < best_th)) { best = sc; best_th = thj; bi = j; bdefl = kind; }
+        best.offer(sc, thj, NH + 1 + j, kind, j);
       }
-      int cert = 1;
-      if (m_unsolved >= 0) {
-        const double rest = fmax(zeta - mass, 0.0) * (1.0 + 1e-8) + 1e-300;
-        double bound;
-        if (a.score_norm == 0) {
-          // every unsolved root lies above the pole left of the smallest unsolved index
-          const double th_lo = m_unsolved > 0 ? S.d[S.J[m_unsolved - 1]] : lower;
-          bound = th_lo > 0.0 ? rest / th_lo : INFINITY;
-        } else {
-          bound = rest;
+      best = block_best(best, s_cand);
+      mass = block_sum(mass, red);
+      const double nsd = block_sum((double)nsolved, red);
+      m_unsolved = block_min(m_unsolved, s_imin);
+      if (tid == 0) {
+        int cert = 1;
+        if (m_unsolved != INT_MAX) {
+          const double rest = fmax(zeta - mass, 0.0) * (1.0 + 1e-8) + 1e-300;
+          double bound;
+          if (a.score_norm == 0) {
+            // every unsolved root lies above the pole left of the smallest unsolved index
+            const double th_lo = m_unsolved > 0 ? S.d[S.J[m_unsolved - 1]] : lower;
+            bound = th_lo > 0.0 ? rest / th_lo : INFINITY;
+          } else {
+            bound = rest;
+          }
+          cert = best.sc * best.sc > bound;
         }
-        cert = best * best > bound;
+        if (phase == 0) atomicAdd(a.diag + 0, (int)nsd);
+        s_cert = cert;
+        s_best = best.idx;
+        s_best_defl = best.kind;
       }
-      if (phase == 0) atomicAdd(a.diag + 0, nsolved);
-      s_cert = cert;
-      s_best = bi;
-      s_best_defl = bdefl;
     }
     __syncthreads();
     if (s_cert) break;
