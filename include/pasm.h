@@ -215,6 +215,14 @@ int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
  * PASM_PROJ_FP64. */
 int pasm_projection_kind(pasm_ctx* ctx, int* kind);
 
+/* Counters of the batched bordered eigensolve (Section 3.1's selection by
+ * secular roots) since the last pasm_init: out[0] = roots solved in the first
+ * window (root 0 and the roots next to lambda^(l)), out[1] = windows whose
+ * Parseval certificate failed (more roots were solved), out[2] = root
+ * iterations that reached their cap.  Synchronises the context's stream.
+ * Errors: PASM_EINVAL, PASM_ESTATE (before pasm_init), PASM_ECUDA. */
+int pasm_secular_stats(pasm_ctx* ctx, int* out);
+
 /* The coarse eigendecomposition computed at setup: Lambda_H (N_H, ascending)
  * and Q (N_H x N_H row-major, column j = eigenvector j, Q^T M_H Q = I); host
  * pointers, either may be NULL. */

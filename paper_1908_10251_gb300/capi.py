@@ -83,6 +83,7 @@ def load_library():
         "pasm_coarse_eigs": (I, [P, P, P]),
         "pasm_project": (I, [P, P, P, P, P]),
         "pasm_projection_kind": (I, [P, ctypes.POINTER(I)]),
+        "pasm_secular_stats": (I, [P, P]),
         "pasm_tiles": (I, [P, I, P]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -233,6 +234,13 @@ def pasm_projection_kind(ctx: Context) -> int:
     kind = ctypes.c_int(-1)
     _check(load_library().pasm_projection_kind(ctx.handle, ctypes.byref(kind)), "pasm_projection_kind")
     return kind.value
+
+
+def pasm_secular_stats(ctx: Context):
+    """(roots solved in the first windows, failed certificates, capped root iterations) since pasm_init."""
+    out = np.zeros(3, dtype=np.int32)
+    _check(load_library().pasm_secular_stats(ctx.handle, out.ctypes.data), "pasm_secular_stats")
+    return tuple(int(v) for v in out)
 
 
 def pasm_sizes(ctx: Context):

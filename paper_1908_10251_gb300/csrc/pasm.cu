@@ -1004,6 +1004,7 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
   }
   // the pair copy of the state U that the first step's gathers read (later steps: the update)
   if (c->opts.precision == PASM_MIXED) to_ff(L, (int64_t)nf * c->ldk, c->U, c->Uff);
+  CK(cudaMemsetAsync(c->diag, 0, sizeof(int) * 8, c->s));  // secular counters count the steps only
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
   c->initialized = true;
@@ -1148,6 +1149,15 @@ int pasm_tiles(pasm_ctx* c, int level, int* chunks_per_thread) {
 int pasm_projection_kind(pasm_ctx* c, int* kind) {
   if (!c || !kind) return PASM_EINVAL;
   *kind = c->proj_tc ? PASM_PROJ_TENSOR : PASM_PROJ_FP64;
+  return PASM_OK;
+}
+
+int pasm_secular_stats(pasm_ctx* c, int* out) {
+  if (!c || !out) return PASM_EINVAL;
+  if (!c->initialized) return PASM_ESTATE;
+  Scope sc(c);
+  CK(cudaMemcpyAsync(out, c->diag, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
   return PASM_OK;
 }
 

@@ -76,6 +76,30 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;
 }
 
+// 1/x for the pole sums, by Newton-Raphson iteration y <- y + y (1 - x y)
+// (quadratic convergence) from a float32 reciprocal of x's leading 24 bits:
+// the seed's relative error (< 2^-22) squares to < 2^-44 after one step and to
+// float64 rounding after the second, so the result is within a few ulp of 1/x.
+// The seed and its widening are formed from the bit fields (integer pipe), so
+// only the four FMAs use the float64 pipe, GB300's scarce one.  Exponents
+// outside 2^(+-120) (where the float32 seed would leave the normal range),
+// zero, Inf and NaN take the float64 division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const int hi = __double2hiint(x);
+  const int e = (hi >> 20) & 0x7FF;
+  if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / x;
+  const unsigned fb = ((unsigned)hi & 0x80000000u) | ((unsigned)(e - 896) << 23) | (((unsigned)hi & 0xFFFFFu) << 3) |
+                      ((unsigned)__double2loint(x) >> 29);
+  const unsigned rb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+  const unsigned re = (rb >> 23) & 0xFFu;
+  double y = __hiloint2double((int)((rb & 0x80000000u) | ((re + 896u) << 20) | ((rb & 0x7FFFFFu) >> 3)),
+                              (int)(rb << 29));
+  double r = fma(-x, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-x, y, 1.0);
+  return fma(y, r, y);
+}
+
 // Sums over the non-deflated poles at theta = origin + tau, split into the
 // poles left of root m (indices t < m) and right of it.  Warp-cooperative.
 __device__ __forceinline__ void secular_sums(const SecShared& S, int nJ, int m, double origin, double tau, int lane,
@@ -83,11 +107,10 @@ __device__ __forceinline__ void secular_sums(const SecShared& S, int nJ, int m, 
   psi = dpsi = phi = dphi = 0.0;
   for (int t = lane; t < nJ; t += 32) {
     const int j = S.J[t];
-    const double r = 1.0 / ((S.d[j] - origin) - tau);
+    const double r = rcp_nr((S.d[j] - origin) - tau);
     const double term = S.w[j] * r;
-    const double dterm = term * r;
-    if (t < m) { psi += term; dpsi += dterm; }
-    else { phi += term; dphi += dterm; }
+    if (t < m) { psi += term; dpsi = fma(term, r, dpsi); }
+    else { phi += term; dphi = fma(term, r, dphi); }
   }
   psi = warp_sum(psi); dpsi = warp_sum(dpsi); phi = warp_sum(phi); dphi = warp_sum(dphi);
 }
@@ -267,7 +290,7 @@ __device__ __forceinline__ void root_vector_sums(const SecShared& S, int nK, int
   ny2 = 0.0; yc = 0.0;
   for (int t = lane; t < nK; t += 32) {
     const int j = S.K[t];
-    const double y = -S.z[j] / ((S.d[S.pole[j]] - origin) - tau);
+    const double y = -S.z[j] * rcp_nr((S.d[S.pole[j]] - origin) - tau);
     ny2 = fma(y, y, ny2);
     yc = fma(y, S.cq[j], yc);
   }

@@ -46,11 +46,14 @@ def main(argv=None):
     wall = (time.perf_counter() - t0) / max(args.steps, 1) * 1e3
     lam = np.zeros(args.k)
     pg.pasm_get(ctx, lam)
+    stats = pg.pasm_secular_stats(ctx)
     trace = pg.pasm_trace_step(ctx)
     launches = pg.pasm_trace_launches(ctx) if args.launches else []
     pg.pasm_destroy(ctx)
     print("n=%d k=%d %s: %.3f ms per step (wall); lambda_1 = %.12g" % (H.fine.n, args.k, args.precision, wall,
                                                                           lam[0]))
+    print("secular: %d window roots, %d failed certificates, %d capped iterations over %d steps"
+          % (stats + (args.steps,)))
     for name, (t_ms, by, fl, n) in sorted(trace.items(), key=lambda kv: -kv[1][0]):
         print("  %-14s %3d launches %8.3f ms %8.1f GB/s" % (name, n, t_ms, by / max(t_ms, 1e-9) / 1e6))
     for name, rows, t_ms, by, fl in launches:

@@ -153,6 +153,24 @@ def test_correction_steps_parity_fp64(pg, use_graph):
         assert np.all(steps == step + 1)
 
 
+def test_secular_counters(pg):
+    """pasm_secular_stats after five config-1 steps: every active pair solved
+    its first window (root 0 and the roots around lambda^(l)) each step, no root
+    iteration hit its cap, and the counters restart at pasm_init."""
+    H = mg.build_hierarchy(2, 64, 8)
+    ctx = setup_ctx(pg, H)
+    k = 8
+    pg.pasm_init(ctx, k, 0.0)
+    assert pg.pasm_secular_stats(ctx) == (0, 0, 0)
+    for _ in range(5):
+        pg.pasm_step(ctx)
+    roots, failed, capped = pg.pasm_secular_stats(ctx)
+    assert roots >= 5 * k * 2 and capped == 0 and failed >= 0
+    pg.pasm_init(ctx, k, 0.0)
+    assert pg.pasm_secular_stats(ctx) == (0, 0, 0)
+    pg.pasm_destroy(ctx)
+
+
 def test_solve_converges_like_oracle(pg):
     """pasm_solve from the coarse initial pairs: the pairs the oracle converges
     (to the brute-force eigenvalues) converge on the GPU to the same values,
