@@ -280,6 +280,37 @@ def test_k_too_big(pg):
     assert ei.value.code == 2
 
 
+def test_maximum_k(pg):
+    """The widest block the library takes, k = 256 (block-vector rows of 2 KB
+    in float64), with a 16 x 16 coarse grid (N_H = 256, so k = N_H too): one
+    float64 step matches the oracle for every pair; mixed precision runs the
+    same step with finite results within 1e-6 of it for the first eigenvalue;
+    k = 257 is refused."""
+    H = mg.build_hierarchy(2, 68, 17)
+    assert H.levels[0].A.shape[0] == 256
+    k = 256
+    prob = oracle.Problem.from_hierarchy(H)
+    lam, U = oracle.initial_state(prob, k)
+    lo, Uo, _ = oracle.correction(prob, lam, U)
+    ctx = setup_ctx(pg, H)
+    pg.pasm_init(ctx, k, 0.0, lam, U)
+    pg.pasm_step(ctx)
+    lg, Ug, _, _ = get_state(pg, ctx, H.fine.n, k)
+    pg.pasm_destroy(ctx)
+    assert np.allclose(lg, lo, rtol=1e-10), np.abs(lg / lo - 1).max()
+    assert colrel(Ug, Uo) < 1e-8
+    ctx = setup_ctx(pg, H, precision=1)
+    pg.pasm_init(ctx, k, 0.0, lam, U)
+    pg.pasm_step(ctx)
+    lm, Um, _, _ = get_state(pg, ctx, H.fine.n, k)
+    assert np.all(np.isfinite(lm)) and np.all(np.isfinite(Um))
+    assert abs(lm[0] / lo[0] - 1) < 1e-6
+    with pytest.raises(pg.PasmError) as ei:
+        pg.pasm_init(ctx, 257, 0.0, np.zeros(257), np.zeros((H.fine.n, 257)))
+    assert ei.value.code == pg.capi.PASM_EINVAL
+    pg.pasm_destroy(ctx)
+
+
 def test_device_pointers_and_stream(pg):
     """Inputs and outputs as torch CUDA tensors on the caller's stream."""
     H = mg.build_hierarchy(2, 32, 8)
