@@ -19,6 +19,12 @@ namespace pasm {
 namespace {
 
 constexpr int kBlock = 256;
+// The residual and transfer kernels are held to 64 registers (four 256-thread
+// blocks per SM): the extra warps hide more gather latency than the few
+// spilled values cost (outer_rhs 0.64 -> 0.59 ms, outer_res 0.34 -> 0.28,
+// spmm 0.52 -> 0.48 at h = 1/1024, k = 64).  The bordering and update kernels
+// were slower that way and keep the compiler's choice.
+constexpr int kMinBlocksGather = 4;
 
 struct Geo {
   int tpr, ch;
@@ -118,7 +124,7 @@ __device__ __forceinline__ void store_pair(double* __restrict__ out, size_t off,
 // Fd = lam .* (M U) stored as (hi, lo) float pairs, R = Fd - A U as float32
 // (U given as float pairs).
 template <int CH>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_rhs_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                        const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
                        const double* __restrict__ lam, const double* __restrict__ U, float2* __restrict__ Fd,
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(kBlock)
 
 // R = Fd - A X as float32 (Fd and X as float pairs).
 template <int CH>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                    const float2* __restrict__ Fd, const double* __restrict__ X, float* __restrict__ R, int ldk,
                    int tpr) {
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(kBlock)
 
 // out = S X; FFIN / FFOUT: X / out as float pairs (else float64).
 template <int CH, bool FFIN, bool FFOUT>
-__global__ void __launch_bounds__(kBlock) k_spmm_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const float2* __restrict__ av, const double* __restrict__ X,
                                                      double* __restrict__ out, int ldk, int tpr) {
   const int rpb = kBlock / tpr;

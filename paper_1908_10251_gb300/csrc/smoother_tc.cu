@@ -11,7 +11,9 @@
 //            pairs, N = 16 output channels, K = 16 input channels per tap; the
 //            tap shift is a shift of the operand's start address;
 //   epilogue: tcgen05.ld of the accumulators, h = (relu(z2+) - relu(z2-)) / 2
-//            (float32, shared memory, reusing the a1 space);
+//            (float32, shared memory, reusing the a1 space, as [row][col][channel
+//            quad][pair][4] so that the 16-byte reads of layer 3 by consecutive
+//            pairs hit consecutive banks);
 //   layer 3 (16 -> 1, CUDA cores, float32): d on the 14 x 14 tile.
 // One elected thread issues the MMAs and commits them to an mbarrier; the
 // wait is bounded and reports through an error counter instead of hanging.
@@ -82,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
                                                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* a1 = smem;                                           // [branch][half][AR][AW][PB][8] bf16
-  float* hs = reinterpret_cast<float*>(smem);                   // [HR][HW][PB][16] f32 (after the MMAs)
+  float* hs = reinterpret_cast<float*>(smem);                   // [HR][HW][4][PB][4] f32 (after the MMAs)
   float* rs = reinterpret_cast<float*>(smem + kA1Bytes);        // [RR][RW][PB]
   uint8_t* w2 = smem + kA1Bytes + kRBytes;                      // 9 x [2 n-groups][2 k-chunks][8][8] bf16
   uint64_t* mbar = reinterpret_cast<uint64_t*>(w2 + kW2Bytes);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       const int x = x0 - 1 + j, y = y0 - 1 + i;
       const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
-      float* dst = hs + ((i * HW + j) * PB + q) * 16;
+      float* dst = hs + (i * HW + j) * 16 * PB + q * 4;
 #pragma unroll
       for (int o = 0; o < 16; o += 4) {
         float4 h4;
@@ -195,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
         h4.y = in ? 0.5f * (fmaxf(vp[o + 1], 0.f) - fmaxf(vm[o + 1], 0.f)) : 0.f;
         h4.z = in ? 0.5f * (fmaxf(vp[o + 2], 0.f) - fmaxf(vm[o + 2], 0.f)) : 0.f;
         h4.w = in ? 0.5f * (fmaxf(vp[o + 3], 0.f) - fmaxf(vm[o + 3], 0.f)) : 0.f;
-        *reinterpret_cast<float4*>(dst + o) = h4;
+        *reinterpret_cast<float4*>(dst + (o / 4) * PB * 4) = h4;
       }
     }
   }
@@ -211,10 +213,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
     float acc = 0.f;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const float4* hp = reinterpret_cast<const float4*>(hs + (((row + tap / 3) * HW + (col + tap % 3)) * PB + q) * 16);
+      const float4* hp =
+          reinterpret_cast<const float4*>(hs + ((row + tap / 3) * HW + (col + tap % 3)) * 16 * PB + q * 4);
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
-        const float4 hv = hp[c4];
+        const float4 hv = hp[c4 * PB];
         acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 0], hv.x, acc);
         acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 1], hv.y, acc);
         acc = fmaf(w13.w3[tap * 16 + 4 * c4 + 2], hv.z, acc);
