@@ -210,8 +210,16 @@ template void jacobi_zero<float>(const Launch&, int, const float*, float, const 
 //
 // Two Jacobi sweeps from a zero guess in one pass:
 //   e1 = w D^-1 f,  e2 = e1 + w D^-1 (f - A e1) = w D^-1 (2 f - A (w D^-1 f)).
+// Float32 sweeps from zero and fused residual-restrictions are held to 64
+// registers (four 256-thread blocks per SM): at h = 1/1024, k = 64 the finest
+// two-sweep kernel went 187 -> 177 us and the level-2 residual-restriction
+// 67 -> 50 us; the other row kernels were as fast or slower that way.  Float64
+// kernels keep the compiler's choice.
+template <typename T> struct MinBlocks { static constexpr int gather = 1; };
+template <> struct MinBlocks<float> { static constexpr int gather = 4; };
+
 template <typename T, int CH>
-__global__ void __launch_bounds__(kBlock) k_jacobi2_zero(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_jacobi2_zero(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                           const T* __restrict__ av, const T* __restrict__ dinv,
                                                           T omega, const T* __restrict__ F, T* __restrict__ out,
                                                           int ldk, int tpr, int prescaled) {
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kBlock) k_jacobi2_zero(int n, const int* __res
 // Residual and restriction in one pass: fc = R (f - A e), the residual of each
 // fine row recomputed for every coarse row that restricts it.
 template <typename T, int CH>
-__global__ void __launch_bounds__(kBlock) k_resid_restrict(int nc, const int* __restrict__ rrp,
+__global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_resid_restrict(int nc, const int* __restrict__ rrp,
                                                             const int* __restrict__ rci, const T* __restrict__ rv,
                                                             const int* __restrict__ arp, const int* __restrict__ aci,
                                                             const T* __restrict__ av, const T* __restrict__ E,

@@ -109,6 +109,7 @@ void coarse_init(const Launch& L, int NH, int k, const double* Q, const double* 
 
 struct SecularArgs {
   int NH, k, ldk;
+  int cs;                 // CTAs per pair: a thread-block cluster sharing the root solves (set by secular_select)
   const double* lamH;     // NH, ascending
   const double* bq;       // NH x ldk: Q^T b
   const double* cq;       // NH x ldk: Q^T c

@@ -31,8 +31,19 @@
 // the weight z_a^2 + z_b^2, the other becomes a deflated root with eigenvector
 // (z_b e_a - z_a e_b) / r; eigenvectors of the remaining roots keep the
 // formula y_j = -z_j / (lambda_j - theta) in the original coordinates.
+//
+// Launch: one thread-block cluster of cs CTAs per pair (cs = 1..4, as many as
+// keep k * cs within the SM count).  Every CTA of the cluster builds the same
+// pole data; the roots of a phase are spread over the cluster's warps, and each
+// solved root is written into every CTA's shared memory (distributed shared
+// memory), so that all CTAs take the same selection and certificate decisions;
+// the cluster barrier orders the exchange.  GB300's float64 pipe (2 FMA per
+// clock and SM) bounds the root solves, so more SMs per pair is more
+// throughput.  Rank 0 alone writes the results.
 #include "common.cuh"
 #include "kernels.cuh"
+
+#include <cooperative_groups.h>
 
 #include <cfloat>
 #include <climits>
@@ -362,11 +373,17 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   __shared__ double s_lower, s_upper;
   __shared__ Cand s_cand[kSecWarps];
   __shared__ int s_imin[kSecWarps];
-  const int i = blockIdx.x;
+  namespace cg = cooperative_groups;
+  const cg::cluster_group cluster = cg::this_cluster();
+  const int cs = a.cs;
+  const int rank = cs > 1 ? (int)cluster.block_rank() : 0;
+  const int i = blockIdx.x / cs;
+  const bool lead = rank == 0;  // the CTA that writes the pair's results
   const int NH = a.NH, ldk = a.ldk;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gwarp = rank * kSecWarps + warp, nwarps = cs * kSecWarps;  // warps of the cluster
   if (!a.active[i]) {
-    if (tid == 0) a.upd[i] = 0;
+    if (tid == 0 && lead) a.upd[i] = 0;
     return;
   }
   SecShared S;
@@ -394,7 +411,7 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
   const double beta = a.beta[i], zeta = a.zeta[i];
   const double zt = zeta - scc;
   if (!(zt > 1e-14 * zeta)) {  // u~ numerically inside V_H: keep the pair for this step
-    if (tid == 0) { a.upd[i] = 0; a.status[i] = ST_DEGENERATE; a.steps[i] += 1; }
+    if (tid == 0 && lead) { a.upd[i] = 0; a.status[i] = ST_DEGENERATE; a.steps[i] += 1; }
     return;
   }
   const double sq = sqrt(zt);
@@ -457,10 +474,12 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     for (int m = max(1, m0 - w); m <= min(nJ, m0 + w); ++m) s_list[nl++] = m;
     if (nl == 1 && nJ == 0) nl = 1;
     s_nlist = nl;
-    a.steps[i] += 1;
+    if (lead) a.steps[i] += 1;
   }
   for (int m = tid; m <= NH; m += kSecThreads) S.solved[m] = 0;
-  __syncthreads();
+  // every CTA of the cluster is running and initialised before any writes into its shared memory
+  if (cs > 1) cluster.sync();
+  else __syncthreads();
   const int nJ = s_nJ, nK = s_nK;
   const double lower = s_lower, upper = s_upper;
 
@@ -468,29 +487,41 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
     // phase 0: root 0 and the window around the root holding lambda^(l);
     // phase 1: every root up to m0 + 8; phase 2: every root
     const int mmax = phase == 0 ? -1 : (phase == 1 ? min(nJ, s_m0 + 8) : nJ);
-    if (phase == 0) {
-      for (int q = warp; q < s_nlist; q += kSecWarps) {
-        const int m = s_list[q];
-        solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
-        double ny2, yc;
-        root_vector_sums(S, nK, m, lane, ny2, yc);
-        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); S.solved[m] = 1; }
+    // a solved root's theta, origin, offset and score go to every CTA of the cluster
+    auto solve_and_publish = [&](int m) {
+      solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
+      double ny2, yc;
+      root_vector_sums(S, nK, m, lane, ny2, yc);
+      if (lane == 0) {
+        const double sbm = (yc + sq) / sqrt(ny2 + 1.0);
+        S.sb[m] = sbm;
+        for (int r = 0; r < cs; ++r) {
+          if (r == rank) continue;
+          *cluster.map_shared_rank(S.theta + m, r) = S.theta[m];
+          *cluster.map_shared_rank(S.orig + m, r) = S.orig[m];
+          *cluster.map_shared_rank(S.tau + m, r) = S.tau[m];
+          *cluster.map_shared_rank(S.sb + m, r) = sbm;
+        }
       }
+    };
+    if (phase == 0) {
+      for (int q = gwarp; q < s_nlist; q += nwarps) solve_and_publish(s_list[q]);
     } else {
-      // warp w takes the w-th, (w+8)-th, ... unsolved root at or below mmax
+      // cluster warp w takes the w-th, (w + nwarps)-th, ... unsolved root at or below mmax
       int cnt = 0;
       for (int m = 0; m <= mmax; ++m) {
         if (S.solved[m]) continue;
-        if ((cnt++ % kSecWarps) != warp) continue;
-        solve_root(S, nJ, m, rho, lower, upper, lane, a.diag + 2);
-        double ny2, yc;
-        root_vector_sums(S, nK, m, lane, ny2, yc);
-        if (lane == 0) { S.sb[m] = (yc + sq) / sqrt(ny2 + 1.0); }
+        if ((cnt++ % nwarps) != gwarp) continue;
+        solve_and_publish(m);
       }
     }
-    __syncthreads();
-    if (phase > 0)
+    if (cs > 1) cluster.sync();
+    else __syncthreads();
+    if (phase == 0) {
+      for (int q = tid; q < s_nlist; q += kSecThreads) S.solved[s_list[q]] = 1;
+    } else {
       for (int m = tid; m <= mmax; m += kSecThreads) S.solved[m] = 1;
+    }
     __syncthreads();
     {
       // best candidate among solved roots and deflated poles: each thread scans
@@ -542,16 +573,19 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
           }
           cert = best.sc * best.sc > bound;
         }
-        if (phase == 0) atomicAdd(a.diag + 0, (int)nsd);
+        if (phase == 0 && lead) atomicAdd(a.diag + 0, (int)nsd);
         s_cert = cert;
         s_best = best.idx;
         s_best_defl = best.kind;
       }
     }
-    __syncthreads();
+    // every CTA has read its copies before the next phase writes new roots into them
+    if (cs > 1) cluster.sync();
+    else __syncthreads();
     if (s_cert) break;
-    if (tid == 0) atomicAdd(a.diag + 1, 1);
+    if (tid == 0 && lead) atomicAdd(a.diag + 1, 1);
   }
+  if (!lead) return;  // no further access to this CTA's shared memory by the cluster
 
   // winner -> alpha and coarse coefficients g (Q basis), a-normalised, sign b(u, u~) > 0
   const int bi = s_best;
@@ -624,9 +658,37 @@ cudaError_t secular_prepare(int NH) {
   return allow_dynamic_smem((const void*)k_secular, secular_smem(NH));
 }
 
-void secular_select(const Launch& L, const SecularArgs& a) {
+// CTAs per pair: as many (up to 4) as keep all of them co-resident on the SMs.
+static int secular_cluster(int k) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  int cs = 1;
+  while (cs < 4 && (size_t)k * (size_t)(cs * 2) <= (size_t)sms) cs *= 2;
+  return cs;
+}
+
+void secular_select(const Launch& L, const SecularArgs& a0) {
+  SecularArgs a = a0;
+  a.cs = secular_cluster(a.k);
   L.begin(KC_SECULAR, (double)a.NH * a.ldk * 8.0 * 3.0, 0.0);
-  k_secular<<<a.k, kSecThreads, secular_smem(a.NH), L.s>>>(a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.k * a.cs));
+  cfg.blockDim = dim3(kSecThreads);
+  cfg.dynamicSmemBytes = secular_smem(a.NH);
+  cfg.stream = L.s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_secular, a);
   L.bump();
 }
 
