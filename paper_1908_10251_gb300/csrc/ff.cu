@@ -288,7 +288,10 @@ __global__ void k_from_ff(int64_t total, const double* __restrict__ in, double* 
 
 // U[row][c] = upd[c] ? alpha[c] X[row][c] + (P W)[row][c] : U[row][c], X as
 // float pairs, W as float pairs (WFF) or float64; identity: P W = W.  Entries
-// of frozen pairs are neither read nor written.
+// of frozen pairs are neither read nor written.  With U null the state is the
+// pair array Usplit alone (the finest-level state of the mixed-precision step;
+// its float64 copy is made on demand), else U is written in float64 and, if
+// Usplit is given, also split into pairs.
 template <int CH, bool WFF>
 __global__ void __launch_bounds__(kBlock)
     k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
@@ -315,19 +318,30 @@ __global__ void __launch_bounds__(kBlock)
     if (!u0 && !u1) continue;  // both pairs frozen: U and its split copy stay as they are
     float xh[2], xl[2];
     load_pair<true>(X, off, xh, xl);
-    double2 u;
-    if (!(u0 && u1)) u = *reinterpret_cast<const double2*>(U + off);
-    double r[2];
+    float h[2], l[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
       float ah, al;
       ff_split(__ldg(alpha + col + v), ah, al);
-      float h = wh[c][v], l = wl[c][v];
-      ff_mac(h, l, ah, al, xh[v], xl[v]);
-      r[v] = ff_to_double(h, l);
+      h[v] = wh[c][v];
+      l[v] = wl[c][v];
+      ff_mac(h[v], l[v], ah, al, xh[v], xl[v]);
+      ff_norm(h[v], l[v]);
     }
-    if (u0) u.x = r[0];
-    if (u1) u.y = r[1];
+    if (!U) {  // the state lives in pairs only: write the updated pairs, keep the frozen one
+      if (!(u0 && u1)) {
+        float oh[2], ol[2];
+        load_pair<true>(Usplit, off, oh, ol);
+        if (!u0) { h[0] = oh[0]; l[0] = ol[0]; }
+        if (!u1) { h[1] = oh[1]; l[1] = ol[1]; }
+      }
+      store_pair<true>(Usplit, off, h, l);
+      continue;
+    }
+    double2 u;
+    if (!(u0 && u1)) u = *reinterpret_cast<const double2*>(U + off);
+    if (u0) u.x = ff_to_double(h[0], l[0]);
+    if (u1) u.y = ff_to_double(h[1], l[1]);
     *reinterpret_cast<double2*>(U + off) = u;
     if (Usplit) {  // the (hi, lo) copy of U the next step's gathers read
       float uh[2], ul[2];

@@ -129,6 +129,9 @@ struct pasm_ctx {
   int launches = 0;
   int last_launches = 0;
   bool initialized = false;
+  // mixed precision: the steps keep the state in Uff (pairs) only, so U (float64)
+  // is out of date after a step until sync_state rebuilds it
+  bool u_stale = false;
 };
 
 extern "C" {
@@ -372,9 +375,10 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
     // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
     if (!u_split) to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
     outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
-    const TopOut first{U, false, X};
+    // x = u + e reads u from its pair copy (in a step the state lives there alone)
+    const TopOut first{c->Uff, true, X};
     T* e = vcycle<T>(c, lt, lt >= 1 ? &first : nullptr);
-    if (e) axpy_ff(L, v.n, U, false, (const float*)e, X, c->ldk);
+    if (e) axpy_ff(L, v.n, c->Uff, true, (const float*)e, X, c->ldk);
     for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
       outer_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RES), v.A, c->Fd, X, (float*)Ftop, c->ldk);
       const TopOut next{X, true, X};
@@ -470,9 +474,11 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
     w_ff = ff;
   }
   const Launch Lu = launcher(c, lt, PASM_TILE_UPDATE);
-  // the finest-level state update also refreshes the pair copy of U for the next step
-  double* usplit = (ff && ps.Uout == c->U && lt == c->nlev - 1) ? c->Uff : nullptr;
-  if (ff) update_pairs_ff(Lu, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd, ps.Uout, usplit, ldk);
+  // the finest-level state update of a mixed-precision step writes the pair copy of U only (the
+  // next step's gathers read it); the float64 U is refreshed from it when read (sync_state)
+  const bool state_pairs = ff && ps.Uout == c->U && lt == c->nlev - 1;
+  if (ff) update_pairs_ff(Lu, lt >= 1 ? &v.P : nullptr, v.n, w, w_ff, X, c->alpha, c->upd,
+                          state_pairs ? nullptr : ps.Uout, state_pairs ? c->Uff : nullptr, ldk);
   else if (lt >= 1) update_pairs(Lu, v.P, w, X, c->alpha, c->upd, ps.Uout, ldk);
   else update_pairs_identity(Lu, v.n, w, X, c->alpha, c->upd, ps.Uout, ldk);
 }
@@ -949,6 +955,14 @@ static int autotune(pasm_ctx* c) {
 }
 }  // extern "C++"
 
+// Rebuild the float64 state U from its pair copy after mixed-precision steps
+// (one elementwise pass, on the context's stream).
+static void sync_state(pasm_ctx* c) {
+  if (!c->u_stale) return;
+  from_ff(launcher(c), (int64_t)c->lv.back().n * c->ldk, c->Uff, c->U);
+  c->u_stale = false;
+}
+
 int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0) {
   if (!c || k < 1 || k > 256 || !(tol >= 0.0)) return PASM_EINVAL;
   if ((lambda0 == nullptr) != (U0 == nullptr)) return PASM_EINVAL;
@@ -1004,6 +1018,7 @@ int pasm_init(pasm_ctx* c, int k, double tol, const double* lambda0, const doubl
   }
   // the pair copy of the state U that the first step's gathers read (later steps: the update)
   if (c->opts.precision == PASM_MIXED) to_ff(L, (int64_t)nf * c->ldk, c->U, c->Uff);
+  c->u_stale = false;
   CK(cudaMemsetAsync(c->diag, 0, sizeof(int) * 8, c->s));  // secular counters count the steps only
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
@@ -1033,6 +1048,7 @@ int pasm_step(pasm_ctx* c, int* n_active) {
     c->last_launches = c->launches;
     CK(cudaGetLastError());
   }
+  if (c->opts.precision == PASM_MIXED) c->u_stale = true;
   if (n_active) {
     CK(cudaStreamSynchronize(c->s));
     *n_active = *c->h_nact;
@@ -1053,7 +1069,11 @@ int pasm_get(pasm_ctx* c, double* lambda, double* U, int* steps, int* status) {
   if (!c || !c->initialized) return PASM_ESTATE;
   Scope sc(c);
   if (lambda) CK(cudaMemcpyAsync(lambda, c->lam, sizeof(double) * c->k, cudaMemcpyDefault, c->s));
-  if (U) { int r = get_block(c, c->U, U, c->lv.back().n); if (r) return r; }
+  if (U) {
+    sync_state(c);
+    int r = get_block(c, c->U, U, c->lv.back().n);
+    if (r) return r;
+  }
   if (steps) CK(cudaMemcpyAsync(steps, c->steps, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
   if (status) CK(cudaMemcpyAsync(status, c->status, sizeof(int) * c->k, cudaMemcpyDefault, c->s));
   int perr = 0;
@@ -1080,6 +1100,7 @@ int pasm_solve(pasm_ctx* c, int k, double tol, const double* lambda0, const doub
 int pasm_bvp(pasm_ctx* c, const double* lambda, const double* U, double* Uhat) {
   if (!c || !c->initialized || !lambda || !U || !Uhat) return PASM_ESTATE;
   Scope sc(c);
+  sync_state(c);  // the pair copy is rebuilt from U below
   const int nf = c->lv.back().n;
   int r = put_lambda(c, lambda, c->lam2);
   if (!r) r = put_block(c, U, c->YM, nf);
@@ -1102,6 +1123,7 @@ int pasm_augmented(pasm_ctx* c, const double* lambda_prev, const double* Uhat, d
                    double* beta, double* zeta) {
   if (!c || !c->initialized || !lambda_prev || !Uhat) return PASM_ESTATE;
   Scope sc(c);
+  sync_state(c);
   const int nf = c->lv.back().n;
   int r = put_lambda(c, lambda_prev, c->lam2);
   if (!r) r = put_block(c, Uhat, c->X, nf);
@@ -1172,6 +1194,7 @@ int pasm_trace_step(pasm_ctx* c, double* ms, double* bytes, double* flops, int* 
   c->launches = 0;
   step_body(c);
   c->tracer = nullptr;
+  if (c->opts.precision == PASM_MIXED) c->u_stale = true;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->s));
   for (int q = 0; q < KC_N; ++q) {
@@ -1380,6 +1403,7 @@ int pasm_nn_capture_residuals(pasm_ctx* c, int level, float* R_out) {
   if (r) return r;
   c->capture_level = level;
   c->capture_buf = c->nn.Rt;
+  sync_state(c);                               // the pair copy is rebuilt from U here
   bvp(c, c->nlev - 1, c->lam, c->U, c->YA);   // scratch output; the pair state is not touched
   c->capture_level = -1;
   c->capture_buf = nullptr;
