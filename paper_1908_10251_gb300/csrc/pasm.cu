@@ -578,13 +578,24 @@ int set_active(pasm_ctx* c, int* active, int* steps, int* status) {
 }
 
 // Copy an n x k user block (host or device, leading dim k) into an n x ldk device block.
+// Block copies between the caller's [n][k] array and the [n][ldk] device block.
+// When k == ldk the rows are contiguous on both sides and one linear copy moves
+// the block (a pitched copy of n short rows runs far below the link's rate).
 int put_block(pasm_ctx* c, const double* src, double* dst, int n) {
+  if (c->k == c->ldk) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n * c->k, cudaMemcpyDefault, c->s));
+    return PASM_OK;
+  }
   CK(cudaMemsetAsync(dst, 0, sizeof(double) * (size_t)n * c->ldk, c->s));
   CK(cudaMemcpy2DAsync(dst, sizeof(double) * c->ldk, src, sizeof(double) * c->k, sizeof(double) * c->k, n,
                        cudaMemcpyDefault, c->s));
   return PASM_OK;
 }
 int get_block(pasm_ctx* c, const double* src, double* dst, int n) {
+  if (c->k == c->ldk) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n * c->k, cudaMemcpyDefault, c->s));
+    return PASM_OK;
+  }
   CK(cudaMemcpy2DAsync(dst, sizeof(double) * c->k, src, sizeof(double) * c->ldk, sizeof(double) * c->k, n,
                        cudaMemcpyDefault, c->s));
   return PASM_OK;
