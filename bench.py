@@ -267,6 +267,10 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
     refset = reference_set(w)
     conv, S = time_to_target(reach, refset, calib_steps)
     missed = [] if refset is None else [int(i) for i in refset if reach[i] < 0]
+    # the paper's stopping quantity at the end of the calibration run, over the counted pairs
+    res = pg.pasm_residuals(ctx)
+    counted = np.where(reach >= 0)[0] if refset is None else np.array([i for i in refset if reach[i] >= 0], dtype=int)
+    res_max = float(res[counted].max()) if counted.size else None
     launches = pg.pasm_last_launches(ctx)
     # timed: W warm-up steps then exactly K steps of the captured graph
     pg.pasm_init(ctx, k, w["tol"])
@@ -304,6 +308,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
             "launches_per_step": launches, "trace": trace, "clocks": cs.summary(), "final_lam": hist[-1].tolist(),
             "fine_jacobi": fine_jacobi, "accepted": accepted, "init_ms": init_ms, "missed": missed,
             "tiles": tiles, "first_init_s": tune_s, "fine_sweep_update": fine_sweep_update,
+            "residual_max": res_max,
             "reached_outside_set": [int(i) for i in np.where(reach >= 0)[0]
                                     if refset is not None and i not in set(refset.tolist())]}
 
@@ -552,6 +557,7 @@ def main_ours(args):
                    "pairs_converged": conv, "pairs": WORK["k"], "steps_to_1e-9": S,
                    "pair_set": "the pairs the float64 oracle drives to 1e-9 on this workload (cluster-aware)",
                    "missed": main["missed"],
+                   "eigen_residual_max": main["residual_max"],
                    "l2": "inputs larger than L2 (536 MB block vectors)", "parallelism": "replicas",
                    "tiles_finest": {kk: v for kk, v in main["tiles"].items() if v},
                    "first_init_s": round(main["first_init_s"], 3)},
@@ -569,6 +575,7 @@ def main_ours(args):
         "variants": {name: {"value": job_value(world, r["converged"], r["S"], r["ms_per_step"], r["init_ms"]),
                             "ms_per_step": r["ms_per_step"], "steps_to_1e-9": r["S"], "init_ms": r["init_ms"],
                             "pairs_converged": r["converged"], "missed": r["missed"], "clocks": r["clocks"],
+                            "eigen_residual_max": r["residual_max"],
                             "learned_steps_accepted": r["accepted"]}
                      for name, r in res.items() if name != primary},
         "setup_s": main["setup_s"],

@@ -215,6 +215,14 @@ int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
  * PASM_PROJ_FP64. */
 int pasm_projection_kind(pasm_ctx* ctx, int* kind);
 
+/* Relative eigen-residuals of the current pairs, the stopping quantity of the
+ * paper's experiments (Section 5) with u scaled to unit M-norm:
+ * res[i] = ||A u_i - lambda_i M u_i||_2 / (|lambda_i| ||u_i||_M), i < k, in
+ * the context's precision (double-float in mixed mode).  Uses the step's
+ * scratch buffers (not during a step); synchronises the context's stream.
+ * Errors: PASM_EINVAL (NULL), PASM_ESTATE (before pasm_init), PASM_ECUDA. */
+int pasm_residuals(pasm_ctx* ctx, double* res);
+
 /* Counters of the batched bordered eigensolve (Section 3.1's selection by
  * secular roots) since the last pasm_init: out[0] = roots solved in the first
  * window (root 0 and the roots next to lambda^(l)), out[1] = windows whose

@@ -84,6 +84,7 @@ def load_library():
         "pasm_project": (I, [P, P, P, P, P]),
         "pasm_projection_kind": (I, [P, ctypes.POINTER(I)]),
         "pasm_secular_stats": (I, [P, P]),
+        "pasm_residuals": (I, [P, P]),
         "pasm_tiles": (I, [P, I, P]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -234,6 +235,14 @@ def pasm_projection_kind(ctx: Context) -> int:
     kind = ctypes.c_int(-1)
     _check(load_library().pasm_projection_kind(ctx.handle, ctypes.byref(kind)), "pasm_projection_kind")
     return kind.value
+
+
+def pasm_residuals(ctx: Context):
+    """Per pair ||A u - lambda M u||_2 / (|lambda| ||u||_M) of the current state (k floats)."""
+    k = pasm_sizes(ctx)[3]
+    out = np.zeros(k, dtype=np.float64)
+    _check(load_library().pasm_residuals(ctx.handle, out.ctypes.data), "pasm_residuals")
+    return out
 
 
 def pasm_secular_stats(ctx: Context):

@@ -548,6 +548,68 @@ __global__ void __launch_bounds__(128) k_colsum(const double* __restrict__ parti
   if (threadIdx.x == 0) out[t] = (red[0] + red[1]) + (red[2] + red[3]);
 }
 
+// Eigen-residual report (the paper's stopping quantity, Section 5): per-block
+// column partials of sum_i r_ij^2 (r = lambda M u - A u, from the outer
+// residual kernel) and sum_i u_ij (lambda M u)_ij, accumulated in float64;
+// layout [block][2][ldk] as for column_sums.  FF: Fd and U hold (hi, lo) float
+// pairs (mixed precision), else float64.  Thread t of a block owns the column
+// pair t % (ldk / 2) on every (kBlock / (ldk / 2))-th row.
+template <typename TR, bool FF>
+__global__ void __launch_bounds__(kBlock) k_residual_partials(int n, int ldk, const TR* __restrict__ R,
+                                                              const double* __restrict__ Fd,
+                                                              const double* __restrict__ U,
+                                                              double* __restrict__ partials) {
+  __shared__ double red[kBlock * 4];
+  const int cpairs = ldk / 2, rpb = kBlock / cpairs;
+  const int cp = threadIdx.x % cpairs, ro = threadIdx.x / cpairs;
+  double rr0 = 0.0, rr1 = 0.0, um0 = 0.0, um1 = 0.0;
+  if (ro < rpb) {
+    for (int row = blockIdx.x * rpb + ro; row < n; row += gridDim.x * rpb) {
+      const size_t off = (size_t)row * ldk + 2 * cp;
+      const double r0 = (double)R[off], r1 = (double)R[off + 1];
+      double m0, m1, u0, u1;
+      if (FF) {
+        const float4 f = *reinterpret_cast<const float4*>(Fd + off);
+        const float4 u = *reinterpret_cast<const float4*>(U + off);
+        m0 = (double)f.x + (double)f.y; m1 = (double)f.z + (double)f.w;
+        u0 = (double)u.x + (double)u.y; u1 = (double)u.z + (double)u.w;
+      } else {
+        m0 = Fd[off]; m1 = Fd[off + 1];
+        u0 = U[off]; u1 = U[off + 1];
+      }
+      rr0 = fma(r0, r0, rr0); rr1 = fma(r1, r1, rr1);
+      um0 = fma(u0, m0, um0); um1 = fma(u1, m1, um1);
+    }
+  }
+  double* mine = red + 4 * threadIdx.x;
+  mine[0] = rr0; mine[1] = rr1; mine[2] = um0; mine[3] = um1;
+  __syncthreads();
+  if (ro == 0) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q < rpb; ++q)
+      for (int e = 0; e < 4; ++e) s[e] += red[4 * (q * cpairs + cp) + e];
+    double* out = partials + (size_t)blockIdx.x * 2 * ldk;
+    out[2 * cp] = s[0]; out[2 * cp + 1] = s[1];
+    out[ldk + 2 * cp] = s[2]; out[ldk + 2 * cp + 1] = s[3];
+  }
+}
+
+template <typename TR>
+int residual_partials(const Launch& L, int n, int ldk, const TR* R, bool ff, const double* Fd, const double* U,
+                      double* partials, int max_blocks) {
+  const int rpb = kBlock / (ldk / 2);
+  const int grid = std::max(1, std::min((n + rpb - 1) / rpb, max_blocks));
+  L.begin(KC_COLSUM, (double)n * ldk * (sizeof(TR) + 16.0), 4.0 * n * ldk);
+  if (ff) k_residual_partials<TR, true><<<grid, kBlock, 0, L.s>>>(n, ldk, R, Fd, U, partials);
+  else k_residual_partials<TR, false><<<grid, kBlock, 0, L.s>>>(n, ldk, R, Fd, U, partials);
+  L.bump();
+  return grid;
+}
+template int residual_partials<float>(const Launch&, int, int, const float*, bool, const double*, const double*,
+                                      double*, int);
+template int residual_partials<double>(const Launch&, int, int, const double*, bool, const double*, const double*,
+                                       double*, int);
+
 void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out) {
   const int width = nq * ldk;
   L.begin(KC_COLSUM, (double)nblk * width * 8.0 + width * 8.0, (double)nblk * width);

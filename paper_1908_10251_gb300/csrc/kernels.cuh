@@ -96,6 +96,11 @@ int border_products(const Launch& L, const DCsr& A, const DCsr& M, const double*
                     double* partials, int ldk, int max_blocks);
 // out[q*ldk + c] = sum_b partials[(b*nq + q)*ldk + c]
 void column_sums(const Launch& L, const double* partials, int nblk, int nq, int ldk, double* out);
+// Per-block column partials [block][2][ldk] of sum r^2 and sum u (lambda M u) (eigen-residual
+// report); returns the number of blocks.
+template <typename TR>
+int residual_partials(const Launch& L, int n, int ldk, const TR* R, bool ff, const double* Fd, const double* U,
+                      double* partials, int max_blocks);
 
 // C (m x ldk) = op(D) (m x p) * B (p x ldk); D row-major with leading dim ldd;
 // trans: op(D) = D^T (then D is p x m).

@@ -1185,6 +1185,38 @@ int pasm_projection_kind(pasm_ctx* c, int* kind) {
   return PASM_OK;
 }
 
+int pasm_residuals(pasm_ctx* c, double* res) {
+  if (!c || !res) return PASM_EINVAL;
+  if (!c->initialized) return PASM_ESTATE;
+  Scope sc(c);
+  const int lt = c->nlev - 1, ldk = c->ldk;
+  LevelDev& v = c->lv[(size_t)lt];
+  const Launch L = launcher(c);
+  int nb;
+  if (c->opts.precision == PASM_MIXED) {
+    outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, c->lam, c->Uff, c->Fd, (float*)v.vF, ldk);
+    nb = residual_partials<float>(L, v.n, ldk, (const float*)v.vF, true, c->Fd, c->Uff, c->partials,
+                                  c->max_border_blocks);
+  } else {
+    outer_rhs_residual<double>(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, c->lam, c->U, c->Fd, (double*)v.vF,
+                               ldk);
+    nb = residual_partials<double>(L, v.n, ldk, (const double*)v.vF, false, c->Fd, c->U, c->partials,
+                                   c->max_border_blocks);
+  }
+  column_sums(L, c->partials, nb, 2, ldk, c->bz);
+  std::vector<double> sums((size_t)2 * ldk), lam((size_t)c->k);
+  CK(cudaMemcpyAsync(sums.data(), c->bz, sizeof(double) * 2 * ldk, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(lam.data(), c->lam, sizeof(double) * c->k, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->s));
+  // |A u - lam M u|_2 / (|lam| |u|_M), with sum u (lam M u) = lam u^T M u
+  for (int i = 0; i < c->k; ++i) {
+    const double rr = sums[(size_t)i], um = sums[(size_t)ldk + i];
+    res[i] = std::sqrt(rr) / std::sqrt(std::fabs(lam[(size_t)i] * um));
+  }
+  return PASM_OK;
+}
+
 int pasm_secular_stats(pasm_ctx* c, int* out) {
   if (!c || !out) return PASM_EINVAL;
   if (!c->initialized) return PASM_ESTATE;

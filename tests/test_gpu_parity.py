@@ -171,6 +171,29 @@ def test_secular_counters(pg):
     pg.pasm_destroy(ctx)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-3)])
+def test_residual_report(pg, precision, tol):
+    """pasm_residuals against the residual of the state pasm_get returns,
+    recomputed on the CPU in float64: ||A u - lam M u|| / (|lam| ||u||_M) per
+    pair, after 1 and after 8 steps (large and small residuals).  Mixed mode
+    forms r in double-float (2^-46 of |A u|), so small residuals agree to
+    1e-3 relative plus 1e-13."""
+    H = mg.build_hierarchy(2, 64, 8)
+    ctx = setup_ctx(pg, H, precision=precision)
+    k = 8
+    pg.pasm_init(ctx, k, 0.0)
+    A, M = H.fine.A, H.fine.M
+    for steps in (1, 7):
+        for _ in range(steps):
+            pg.pasm_step(ctx)
+        res = pg.pasm_residuals(ctx)
+        lam, U, _, _ = get_state(pg, ctx, H.fine.n, k)
+        R = A @ U - (M @ U) * lam
+        ref = np.linalg.norm(R, axis=0) / (np.abs(lam) * np.sqrt(np.einsum("ij,ij->j", U, M @ U)))
+        assert np.all(np.abs(res - ref) <= tol * ref + 1e-13), (res, ref)
+    pg.pasm_destroy(ctx)
+
+
 def test_solve_converges_like_oracle(pg):
     """pasm_solve from the coarse initial pairs: the pairs the oracle converges
     (to the brute-force eigenvalues) converge on the GPU to the same values,
