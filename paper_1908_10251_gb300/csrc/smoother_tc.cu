@@ -31,7 +31,9 @@ constexpr int HW = TW + 2, HR = TR + 2;  // h tile: 16 x 16 (one 128-row MMA blo
 constexpr int AW = TW + 4, AR = TR + 4;  // a1 tile: 18 x 18
 constexpr int RW = TW + 6, RR = TR + 6;  // r tile: 20 x 20
 constexpr int PB = 8;                    // pairs per CTA
-constexpr int kThreads = 256;            // 8 warps: two per TMEM lane quarter
+constexpr int kThreads = 512;            // 16 warps: four per TMEM lane quarter (one CTA per SM,
+                                         // so the warps of each phase are all there is to hide latency)
+constexpr int kWarpsPerQuarter = kThreads / 128;
 
 constexpr int kPlane = AR * AW * PB * 16;          // bytes of one channel half of one branch
 constexpr int kA1Bytes = 4 * kPlane;               // 2 branches x 2 halves
@@ -133,11 +135,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
     const int pix = (row * AW + col) * PB + q;  // 16-byte row index inside a plane
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-      __align__(16) __nv_bfloat16 vp[8], vm[8];
+      __align__(16) __nv_bfloat162 vp[4], vm[4];  // two channels per conversion
 #pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        vp[o] = __float2bfloat16_rn(fmaxf(z[half * 8 + o], 0.f));
-        vm[o] = __float2bfloat16_rn(fmaxf(-z[half * 8 + o], 0.f));
+      for (int o = 0; o < 4; ++o) {
+        const float za = z[half * 8 + 2 * o], zb = z[half * 8 + 2 * o + 1];
+        vp[o] = __floats2bfloat162_rn(fmaxf(za, 0.f), fmaxf(zb, 0.f));
+        vm[o] = __floats2bfloat162_rn(fmaxf(-za, 0.f), fmaxf(-zb, 0.f));
       }
       *reinterpret_cast<uint4*>(a1 + (0 * 2 + half) * kPlane + pix * 16) = *reinterpret_cast<uint4*>(vp);
       *reinterpret_cast<uint4*>(a1 + (1 * 2 + half) * kPlane + pix * 16) = *reinterpret_cast<uint4*>(vm);
@@ -177,11 +180,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (done) {
     // epilogue: TMEM lane m = 32 * (warp % 4) + lane = (h pixel j, pair q) with m = j * PB + q;
-    // the two warps of a lane quarter take alternate h rows
-    const int quarter = warp & 3, half = warp >> 2;
+    // the warps of a lane quarter take every kWarpsPerQuarter-th h row
+    const int quarter = warp & 3, rowgrp = warp >> 2;
     const int m = quarter * 32 + lane;
     const int j = m / PB, q = m % PB;
-    for (int i = half; i < HR; i += 2) {
+    for (int i = rowgrp; i < HR; i += kWarpsPerQuarter) {
       float vp[16], vm[16];
       const uint32_t lanebase = tmem + ((uint32_t)(quarter * 32) << 16);
       tmem_ld16(lanebase + (uint32_t)((i * 2 + 0) * 16), vp);

@@ -25,6 +25,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "cg"])
     ap.add_argument("--launches", action="store_true", help="also list every launch of the traced step")
+    ap.add_argument("--learned", action="store_true",
+                    help="mixed precision with the learned post-smoothing step on every 2D grid (seeded random weights)")
     args = ap.parse_args(argv)
 
     import torch
@@ -36,7 +38,17 @@ def main(argv=None):
     stream = torch.cuda.current_stream()
     opts = pg.pasm_default_opts(precision=pg.PASM_MIXED if args.precision == "mixed" else pg.PASM_FP64,
                                 smoother=pg.PASM_CG if args.smoother == "cg" else pg.PASM_JACOBI)
+    if args.learned:
+        opts = pg.pasm_default_opts(precision=pg.PASM_MIXED, smoother=1)
     ctx = pg.pasm_setup([lv.A for lv in H.levels], [lv.M for lv in H.levels], H.P, opts, stream.cuda_stream)
+    if args.learned:
+        # He-style random weights of the 1 -> 16 -> 16 -> 1 network (the kernels' cost does not depend on them)
+        rng = np.random.default_rng(0)
+        w = [rng.standard_normal(sh) * np.sqrt(2.0 / (sh[0] * sh[1] * sh[2]))
+             for sh in ((3, 3, 1, 16), (3, 3, 16, 16), (3, 3, 16, 1))]
+        w[2] *= 0.1
+        pg.pasm_nn_setup(ctx, np.array([lv.N - 1 for lv in H.levels], dtype=np.int32),
+                         np.concatenate([x.ravel() for x in w]).astype(np.float32))
     pg.pasm_init(ctx, args.k, 0.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
