@@ -108,13 +108,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
     const int off = tap * 512 + (co % 8) * 16 + (co / 8) * 256 + (ci / 8) * 128 + (ci % 8) * 2;
     *reinterpret_cast<__nv_bfloat16*>(w2 + off) = __float2bfloat16_rn(W[144 + t]);
   }
-  // residual tile with a 3-pixel halo (zero outside the grid and for padded pairs)
-  for (int t = tid; t < RR * RW * PB; t += kThreads) {
-    const int q = t % PB, col = (t / PB) % RW, row = t / (PB * RW);
-    const int x = x0 - 3 + col, y = y0 - 3 + row, c = c0 + q;
-    float v = 0.f;
-    if (x >= 0 && x < nx && y >= 0 && y < ny && c < k) v = R[((int64_t)y * nx + x) * ldk + c];
-    rs[t] = v;
+  // residual tile with a 3-pixel halo (zero outside the grid and for padded pairs).  A block of 8
+  // real pairs is one 32-byte segment per pixel: two 16-byte asynchronous copies (cp.async, all in
+  // flight at once), zero-filled outside the grid; a block with padded pairs loads element-wise.
+  if (c0 + PB <= k) {
+    for (int t = tid; t < RR * RW * 2; t += kThreads) {
+      const int hlf = t & 1, col = (t >> 1) % RW, row = (t >> 1) / RW;
+      const int x = x0 - 3 + col, y = y0 - 3 + row;
+      const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
+      const float* src = in ? R + ((int64_t)y * nx + x) * ldk + c0 + 4 * hlf : R;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(rs + (row * RW + col) * PB + 4 * hlf)),
+                   "l"(src), "r"(in ? 16 : 0));
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    for (int t = tid; t < RR * RW * PB; t += kThreads) {
+      const int q = t % PB, col = (t / PB) % RW, row = t / (PB * RW);
+      const int x = x0 - 3 + col, y = y0 - 3 + row, c = c0 + q;
+      float v = 0.f;
+      if (x >= 0 && x < nx && y >= 0 && y < ny && c < k) v = R[((int64_t)y * nx + x) * ldk + c];
+      rs[t] = v;
+    }
   }
   __syncthreads();
   // layer 1 on the 18 x 18 tile: a1+- as bf16, zero outside the grid
@@ -156,14 +170,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
   if (tid == 0) {
     // kind::f16, D f32, A and B bf16, both K-major, N = 16, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    const uint32_t a1base = smem_u32(a1), w2base = smem_u32(w2);
+    // The descriptors are formed once: the start-address field holds (address >> 4) in 14 bits, and
+    // every operand here lies below 2^18 bytes, so shifting an operand by `off` bytes adds off >> 4.
+    const uint64_t a0 = smem_desc(smem_u32(a1), kPlane, PB * 16);
+    const uint64_t b0 = smem_desc(smem_u32(w2), 128, 256);
     for (int i = 0; i < HR; ++i)
       for (int b = 0; b < 2; ++b) {
         const uint32_t dcol = tmem + (uint32_t)((i * 2 + b) * 16);
+        const uint64_t ai = a0 + (uint64_t)((b * 2 * kPlane + i * AW * PB * 16) >> 4);
+#pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
           const int dy = tap / 3, dx = tap % 3;  // a1 row i + dy, col j + dx for h pixel (i, j)
-          const uint32_t aaddr = a1base + (uint32_t)(b * 2 * kPlane) + (uint32_t)(((i + dy) * AW + dx) * PB * 16);
-          mma_bf16(dcol, smem_desc(aaddr, kPlane, PB * 16), smem_desc(w2base + tap * 512, 128, 256), idesc,
+          mma_bf16(dcol, ai + (uint64_t)(((dy * AW + dx) * PB * 16) >> 4), b0 + (uint64_t)(tap * 512 >> 4), idesc,
                    tap > 0 ? 1u : 0u);
         }
       }
