@@ -58,7 +58,7 @@ def test_cg_bvp_parity_fp64(pg, dim, Nf, Nc, k, nu):
 
 
 def test_cg_correction_steps_parity_fp64(pg):
-    """Config-1 shape (h = 1/64, H = 1/8, k = 8): five CG-smoothed correction
+    """The small unit-square workload (h = 1/64, H = 1/8, k = 8): five CG-smoothed correction
     steps from the same initial pairs match the oracle step by step."""
     H = mg.build_hierarchy(2, 64, 8)
     ctx = setup_ctx(pg, H, precision=0)

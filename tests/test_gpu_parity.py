@@ -136,7 +136,7 @@ def test_augmented_step_parity(pg, Nf, Nc, k):
 
 @pytest.mark.parametrize("use_graph", [1, 0])
 def test_correction_steps_parity_fp64(pg, use_graph):
-    """Config-1 shape (h = 1/64, H = 1/8, k = 8): five correction steps from the
+    """The small unit-square workload (h = 1/64, H = 1/8, k = 8): five correction steps from the
     same initial pairs match the oracle step by step."""
     H = mg.build_hierarchy(2, 64, 8)
     ctx = setup_ctx(pg, H, use_graph=use_graph)
@@ -154,7 +154,7 @@ def test_correction_steps_parity_fp64(pg, use_graph):
 
 
 def test_secular_counters(pg):
-    """pasm_secular_stats after five config-1 steps: every active pair solved
+    """pasm_secular_stats after five steps at h = 1/64, H = 1/8, k = 8: every active pair solved
     its first window (root 0 and the roots around lambda^(l)) each step, no root
     iteration hit its cap, and the counters restart at pasm_init."""
     H = mg.build_hierarchy(2, 64, 8)
