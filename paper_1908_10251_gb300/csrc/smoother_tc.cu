@@ -1,12 +1,12 @@
 // Fused forward pass of the learned post-smoother on the 5th-generation tensor
-// cores (tcgen05, sm_103a): one CTA computes N(r) on a 14 x 14 output tile of 8
-// pairs, keeping every activation on chip.
+// cores (tcgen05, sm_103a): one CTA computes N(r) on a 14 x 6 output tile of 8
+// pairs, keeping every activation on chip; two CTAs share an SM.
 //
-//   layer 1 (1 -> 16, CUDA cores, float32): z1 on the 18 x 18 halo tile,
+//   layer 1 (1 -> 16, CUDA cores, float32): z1 on the 18 x 10 halo tile,
 //            a1+ = relu(z1), a1- = relu(-z1) stored as bf16 in shared memory in
 //            the canonical K-major layout of the tensor-core operand;
 //   layer 2 (16 -> 16, tcgen05.mma kind::f16, bf16 x bf16 -> f32 in TMEM):
-//            for each of the 16 rows of the 16 x 16 tile of h, both branches,
+//            for each of the 8 rows of the 16 x 8 tile of h, both branches,
 //            an implicit GEMM over the 9 taps: M = 128 rows = 16 pixels x 8
 //            pairs, N = 16 output channels, K = 16 input channels per tap; the
 //            tap shift is a shift of the operand's start address;
@@ -14,7 +14,7 @@
 //            (float32, shared memory, reusing the a1 space, as [row][col][channel
 //            quad][pair][4] so that the 16-byte reads of layer 3 by consecutive
 //            pairs hit consecutive banks);
-//   layer 3 (16 -> 1, CUDA cores, float32): d on the 14 x 14 tile.
+//   layer 3 (16 -> 1, CUDA cores, float32): d on the 14 x 6 tile.
 // One elected thread issues the MMAs and commits them to an mbarrier; the
 // wait is bounded and reports through an error counter instead of hanging.
 #include "common.cuh"
@@ -26,13 +26,15 @@
 namespace pasm {
 namespace {
 
-constexpr int TW = 14, TR = 14;          // output tile (pixels)
-constexpr int HW = TW + 2, HR = TR + 2;  // h tile: 16 x 16 (one 128-row MMA block per row)
-constexpr int AW = TW + 4, AR = TR + 4;  // a1 tile: 18 x 18
-constexpr int RW = TW + 6, RR = TR + 6;  // r tile: 20 x 20
+// Output tile 14 x 6 pixels: 105 KB of shared memory and 256 TMEM columns, so two CTAs share an SM
+// and one CTA's MMAs, loads and CUDA-core layers overlap the other's.
+constexpr int TW = 14, TR = 6;           // output tile (pixels)
+constexpr int HW = TW + 2, HR = TR + 2;  // h tile: 16 x 8 (one 128-row MMA block per row)
+constexpr int AW = TW + 4, AR = TR + 4;  // a1 tile: 18 x 10
+constexpr int RW = TW + 6, RR = TR + 6;  // r tile: 20 x 12
 constexpr int PB = 8;                    // pairs per CTA
-constexpr int kThreads = 512;            // 16 warps: four per TMEM lane quarter (one CTA per SM,
-                                         // so the warps of each phase are all there is to hide latency)
+constexpr int kThreads = 512;            // 16 warps: four per TMEM lane quarter
+constexpr int kCtasPerSm = 2;
 constexpr int kWarpsPerQuarter = kThreads / 128;
 
 constexpr int kPlane = AR * AW * PB * 16;          // bytes of one channel half of one branch
@@ -43,7 +45,8 @@ constexpr int kW2Bytes = 9 * 512;                  // bf16, canonical K-major, p
 constexpr int kSmem = kA1Bytes + kRBytes + kW2Bytes + 16;
 static_assert(kHBytes <= kA1Bytes, "h must fit in the a1 space");
 static_assert(HW * PB == 128, "one MMA block per h row");
-constexpr uint32_t kTmemCols = 512;                // 16 rows x 2 branches x 16 columns
+constexpr uint32_t kTmemCols = HR * 2 * 16;        // h rows x 2 branches x 16 columns
+static_assert(kTmemCols == 256 && kSmem * kCtasPerSm <= 227 * 1024, "two CTAs per SM");
 constexpr int kWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -80,7 +83,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 // Layers 1 and 3 (CUDA cores) read their weights from the kernel's parameter
 // space: every FMA takes its weight as a constant-bank operand, no load.
-__global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, int k, int tiles_x,
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, int ldk, int k, int tiles_x,
                                                        const NNOuterWeights w13, const float* __restrict__ W,
                                                        const float* __restrict__ R, float* __restrict__ D,
                                                        int* __restrict__ err) {
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
     }
   }
   __syncthreads();
-  // layer 1 on the 18 x 18 tile: a1+- as bf16, zero outside the grid
+  // layer 1 on the 18 x 10 tile: a1+- as bf16, zero outside the grid
   for (int t = tid; t < AR * AW * PB; t += kThreads) {
     const int q = t % PB, col = (t / PB) % AW, row = t / (PB * AW);
     const int x = x0 - 2 + col, y = y0 - 2 + row;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_nn_tc(int nx, int ny, int ldk, 
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
   if (!done) return;
-  // layer 3 on the 14 x 14 tile
+  // layer 3 on the 14 x 6 tile
   for (int t = tid; t < TR * TW * PB; t += kThreads) {
     const int q = t % PB, col = (t / PB) % TW, row = t / (PB * TW);
     const int x = x0 + col, y = y0 + row, c = c0 + q;

@@ -161,7 +161,7 @@ def test_trained_smoother_beats_jacobi_on_held_out_residuals(pg):
 def test_tensor_core_forward_parity(pg):
     """Fused tcgen05 forward (layer 2 in bf16 on the tensor cores, float32
     accumulation) against the oracle with the same bf16 rounding of layer 2's
-    inputs; tiles of 14 x 14 pixels x 8 pairs, a grid that is not a multiple of
+    inputs; tiles of 14 x 6 pixels x 8 pairs, a grid that is not a multiple of
     the tile (31 x 31) and a padded pair block (k = 5 of 8)."""
     w = sm.init_weights(3).astype(np.float32).astype(np.float64) * 2.0
     H, grids, ctx = make(pg, learned=True, w=w)
