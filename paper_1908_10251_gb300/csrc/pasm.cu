@@ -112,6 +112,7 @@ struct pasm_ctx {
     int* accepted = nullptr;
     int* err = nullptr;                      // timed-out tensor-core waits
     NNOuterWeights w13{};                    // host copy of layers 1 and 3 (kernel parameters)
+    uint16_t* w2 = nullptr;                  // layer 2 as bf16 in the tensor-core operand layout
     std::vector<void*> allocs;
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
@@ -281,7 +282,7 @@ int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
   NNGrid g{nn.nx[l], nn.ny[l], ldk, c->k};
   const float om = (float)c->opts.omega;
   rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, nn.R, ldk);        // r = f - A e
-  if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.w13, nn.W, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
+  if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.w13, nn.w2, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
   else nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
   nn_add(L, (int64_t)v.n * ldk, cur, nn.D, nn.X);                                 // e + d
   rowop<float>(L, OP_RESID, v.A, nn.X, F, nullptr, nullptr, om, nn.Rt, ldk);      // f - A (e + d)
@@ -1298,6 +1299,11 @@ static int nn_refresh_host_weights(pasm_ctx* c) {
   CK(cudaMemcpy(h.data(), c->nn.W, sizeof(float) * kNNWeights, cudaMemcpyDeviceToHost));
   std::memcpy(c->nn.w13.w1, h.data(), sizeof(float) * 144);
   std::memcpy(c->nn.w13.w3, h.data() + 144 + 2304, sizeof(float) * 144);
+  if (c->nn.w2) {
+    std::vector<uint16_t> w2((size_t)2304);
+    nn_tc_layer2_layout(h.data() + 144, w2.data());
+    CK(cudaMemcpy(c->nn.w2, w2.data(), sizeof(uint16_t) * 2304, cudaMemcpyHostToDevice));
+  }
   return PASM_OK;
 }
 
@@ -1323,6 +1329,7 @@ int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
     AL(nn.allocs, &nn.buf.wflip2, 2304); AL(nn.allocs, &nn.buf.wflip3, 144);
     AL(nn.allocs, &nn.norms, 2 * 256); AL(nn.allocs, &nn.loss, 1); AL(nn.allocs, &nn.accepted, 256);
     AL(nn.allocs, &nn.err, 4);
+    AL(nn.allocs, &nn.w2, 2304);
     CK(cudaMemset(nn.err, 0, sizeof(int) * 4));
   }
   CK(cudaMemcpy(nn.W, weights, sizeof(float) * kNNWeights, cudaMemcpyDefault));
@@ -1374,7 +1381,7 @@ int pasm_nn_apply(pasm_ctx* c, int level, int k, const float* R, float* D) {
   if (r) return r;
   NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
   if (c->opts.smoother == PASM_LEARNED && nn_tc_supported(ldk2))
-    nn_forward_tc(launcher(c), g, nn.w13, nn.W, nn.R, nn.D, nn.err);
+    nn_forward_tc(launcher(c), g, nn.w13, nn.w2, nn.R, nn.D, nn.err);
   else
     nn_forward(launcher(c), g, nn.buf, nn.W, nn.R, nn.D);
   CK(cudaMemcpy2DAsync(D, sizeof(float) * k, nn.D, sizeof(float) * ldk2, sizeof(float) * k, n, cudaMemcpyDefault,

@@ -44,15 +44,17 @@ void nn_select(const Launch& L, int n, int ldk, const float* E, const float* D, 
 // (bf16 operands, float32 accumulation); needs ldk % 8 == 0.  A timed-out wait
 // increments *err and leaves D unwritten for that tile.
 // The CUDA-core weights of layers 1 (1 -> 16) and 3 (16 -> 1), passed by value
-// so that the kernel reads them from its parameter space; W (device) still
-// supplies layer 2.  A host copy must track every change of W.
+// so that the kernel reads them from its parameter space; layer 2 comes from a
+// device copy already in the tensor-core operand layout (nn_tc_layer2_layout,
+// 4608 bytes).  Both host-side forms must track every change of W.
 struct NNOuterWeights {
   float w1[144];  // [tap][out]
   float w3[144];  // [tap][in]
 };
 cudaError_t nn_tc_prepare();
 bool nn_tc_supported(int ldk);
-void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const float* W, const float* R,
+void nn_tc_layer2_layout(const float* W2, uint16_t* out);  // 2304 floats -> 2304 bf16 (4608 bytes)
+void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const void* w2, const float* R,
                    float* D, int* err);
 
 }  // namespace pasm

@@ -23,6 +23,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <cstring>
+
 namespace pasm {
 namespace {
 
@@ -84,7 +86,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // Layers 1 and 3 (CUDA cores) read their weights from the kernel's parameter
 // space: every FMA takes its weight as a constant-bank operand, no load.
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, int ldk, int k, int tiles_x,
-                                                       const NNOuterWeights w13, const float* __restrict__ W,
+                                                       const NNOuterWeights w13, const uint8_t* __restrict__ w2g,
                                                        const float* __restrict__ R, float* __restrict__ D,
                                                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -105,12 +107,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, 
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // W2 as bf16 in the canonical layout (row n = output channel, k = input channel)
-  for (int t = tid; t < 2304; t += kThreads) {
-    const int tap = t / 256, ci = (t / 16) % 16, co = t % 16;   // W2[tap][ci][co]
-    const int off = tap * 512 + (co % 8) * 16 + (co / 8) * 256 + (ci / 8) * 128 + (ci % 8) * 2;
-    *reinterpret_cast<__nv_bfloat16*>(w2 + off) = __float2bfloat16_rn(W[144 + t]);
-  }
+  // W2, already bf16 in the canonical layout (nn_tc_layer2_layout), by 16-byte asynchronous copies
+  for (int t = tid; t < kW2Bytes / 16; t += kThreads)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(w2 + 16 * t)), "l"(w2g + 16 * t));
   // residual tile with a 3-pixel halo (zero outside the grid and for padded pairs).  A block of 8
   // real pairs is one 32-byte segment per pixel: two 16-byte asynchronous copies (cp.async, all in
   // flight at once), zero-filled outside the grid; a block with padded pairs loads element-wise.
@@ -123,7 +122,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, 
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(rs + (row * RW + col) * PB + 4 * hlf)),
                    "l"(src), "r"(in ? 16 : 0));
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
   } else {
     for (int t = tid; t < RR * RW * PB; t += kThreads) {
       const int q = t % PB, col = (t / PB) % RW, row = t / (PB * RW);
@@ -133,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, 
       rs[t] = v;
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // layer 1 on the 18 x 10 tile: a1+- as bf16, zero outside the grid
   for (int t = tid; t < AR * AW * PB; t += kThreads) {
@@ -254,19 +253,35 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_nn_tc(int nx, int ny, 
 
 }  // namespace
 
+// Layer 2's weights W2[tap][ci][co] (2304 floats) as bf16 (round to nearest even) in the kernel's
+// canonical K-major operand layout: row n = output channel, k = input channel, per tap two 8 x 8
+// core matrices along n (256 B apart) and two along k (128 B apart).
+void nn_tc_layer2_layout(const float* W2, uint16_t* out) {
+  for (int t = 0; t < 2304; ++t) {
+    const int tap = t / 256, ci = (t / 16) % 16, co = t % 16;
+    const int off = tap * 512 + (co % 8) * 16 + (co / 8) * 256 + (ci / 8) * 128 + (ci % 8) * 2;
+    uint32_t u;
+    std::memcpy(&u, W2 + t, sizeof(u));
+    uint16_t b;
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x7FFFFFu)) b = (uint16_t)((u >> 16) | 0x40u);  // NaN
+    else b = (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+    out[off / 2] = b;
+  }
+}
+
 cudaError_t nn_tc_prepare() {
   return cudaFuncSetAttribute(k_nn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
 }
 
 bool nn_tc_supported(int ldk) { return ldk % PB == 0; }
 
-void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const float* W, const float* R,
+void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const void* w2, const float* R,
                    float* D, int* err) {
   const int tiles_x = (g.nx + TW - 1) / TW, tiles_y = (g.ny + TR - 1) / TR;
   dim3 grid(tiles_x * tiles_y, g.ldk / PB);
   const double pix = (double)g.nx * g.ny * g.ldk;
   L.begin(KC_NN, pix * 8.0, pix * 2.0 * (2 * 9 * 16 + 2 * 9 * 256 + 9 * 16));
-  k_nn_tc<<<grid, kThreads, kSmem, L.s>>>(g.nx, g.ny, g.ldk, g.k, tiles_x, w13, W, R, D, err);
+  k_nn_tc<<<grid, kThreads, kSmem, L.s>>>(g.nx, g.ny, g.ldk, g.k, tiles_x, w13, (const uint8_t*)w2, R, D, err);
   L.bump();
 }
 
