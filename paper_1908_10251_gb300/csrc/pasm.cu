@@ -284,8 +284,7 @@ int post_hooks(pasm_ctx* c, int l, float* cur, float* tmp, float* F) {
   rowop<float>(L, OP_RESID, v.A, cur, F, nullptr, nullptr, om, nn.R, ldk);        // r = f - A e
   if (nn_tc_supported(ldk)) nn_forward_tc(L, g, nn.w13, nn.w2, nn.R, nn.D, nn.err);        // d = N(r), tensor cores
   else nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
-  nn_add(L, (int64_t)v.n * ldk, cur, nn.D, nn.X);                                 // e + d
-  rowop<float>(L, OP_RESID, v.A, nn.X, F, nullptr, nullptr, om, nn.Rt, ldk);      // f - A (e + d)
+  rowop<float>(L, OP_RESID, v.A, nn.D, nn.R, nullptr, nullptr, om, nn.Rt, ldk);   // f - A (e + d) = r - A d
   nn_column_norms(L, v.n, ldk, nn.R, nn.Rt, nn.partial, nn.norms);
   nn_select(L, v.n, ldk, cur, nn.D, nn.R, v.dinv32, om, nn.norms, tmp, nn.accepted);
   return 1;
