@@ -68,7 +68,7 @@ __device__ __forceinline__ void load_pair(const double* __restrict__ X, size_t o
 
 // acc += a_p X[ci_p, cols] for the N entries p .. p+N-1: index and value loads,
 // then the N row gathers, then the double-float products.
-template <int CH, int N, bool FFIN>
+template <int CH, int N, bool FFIN, bool EX>
 __device__ __forceinline__ void gather_group_ff(const int* __restrict__ ci, const float2* __restrict__ av,
                                                 const double* __restrict__ X, int p, int lane, int tpr, int ldk,
                                                 float (&hi)[CH][2], float (&lo)[CH][2]) {
@@ -89,11 +89,15 @@ __device__ __forceinline__ void gather_group_ff(const int* __restrict__ ci, cons
 #pragma unroll
     for (int c = 0; c < CH; ++c)
 #pragma unroll
-      for (int v = 0; v < 2; ++v) ff_mac(hi[c][v], lo[c][v], a[u].x, a[u].y, xh[u][c][v], xl[u][c][v]);
+      for (int v = 0; v < 2; ++v) {
+        if (EX) ff_mac_exact(hi[c][v], lo[c][v], a[u].x, xh[u][c][v], xl[u][c][v]);
+        else ff_mac(hi[c][v], lo[c][v], a[u].x, a[u].y, xh[u][c][v], xl[u][c][v]);
+      }
 }
 
-// One row of S X in double-float (groups of 4 entries, then an exact remainder group).
-template <int CH, bool FFIN>
+// One row of S X in double-float (groups of 4 entries, then an exact remainder group);
+// EX: S's values are float32 (no low parts).
+template <int CH, bool FFIN, bool EX = false>
 __device__ __forceinline__ void gather_row_ff(const int* __restrict__ rp, const int* __restrict__ ci,
                                               const float2* __restrict__ av, const double* __restrict__ X, int row,
                                               int lane, int tpr, int ldk, float (&hi)[CH][2], float (&lo)[CH][2]) {
@@ -101,11 +105,11 @@ __device__ __forceinline__ void gather_row_ff(const int* __restrict__ rp, const 
   for (int c = 0; c < CH; ++c) hi[c][0] = hi[c][1] = lo[c][0] = lo[c][1] = 0.f;
   int p = __ldg(rp + row);
   const int p1 = __ldg(rp + row + 1);
-  for (; p + 4 <= p1; p += 4) gather_group_ff<CH, 4, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  for (; p + 4 <= p1; p += 4) gather_group_ff<CH, 4, FFIN, EX>(ci, av, X, p, lane, tpr, ldk, hi, lo);
   const int rem = p1 - p;
-  if (rem == 3) gather_group_ff<CH, 3, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
-  else if (rem == 2) gather_group_ff<CH, 2, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
-  else if (rem == 1) gather_group_ff<CH, 1, FFIN>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  if (rem == 3) gather_group_ff<CH, 3, FFIN, EX>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  else if (rem == 2) gather_group_ff<CH, 2, FFIN, EX>(ci, av, X, p, lane, tpr, ldk, hi, lo);
+  else if (rem == 1) gather_group_ff<CH, 1, FFIN, EX>(ci, av, X, p, lane, tpr, ldk, hi, lo);
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     ff_norm(hi[c][0], lo[c][0]);
@@ -123,7 +127,7 @@ __device__ __forceinline__ void store_pair(double* __restrict__ out, size_t off,
 
 // Fd = lam .* (M U) stored as (hi, lo) float pairs, R = Fd - A U as float32
 // (U given as float pairs).
-template <int CH>
+template <int CH, bool AEX>
 __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_rhs_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                        const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
   if (row >= n) return;
   float muh[CH][2], mul[CH][2], auh[CH][2], aul[CH][2];
   gather_row_ff<CH, true>(mrp, mci, mval, U, row, lane, tpr, ldk, muh, mul);
-  gather_row_ff<CH, true>(arp, aci, aval, U, row, lane, tpr, ldk, auh, aul);
+  gather_row_ff<CH, true, AEX>(arp, aci, aval, U, row, lane, tpr, ldk, auh, aul);
   const size_t base = (size_t)row * ldk;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
 }
 
 // R = Fd - A X as float32 (Fd and X as float pairs).
-template <int CH>
+template <int CH, bool AEX>
 __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                    const float2* __restrict__ Fd, const double* __restrict__ X, float* __restrict__ R, int ldk,
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
   const int lane = threadIdx.x % tpr;
   if (row >= n) return;
   float axh[CH][2], axl[CH][2];
-  gather_row_ff<CH, true>(arp, aci, aval, X, row, lane, tpr, ldk, axh, axl);
+  gather_row_ff<CH, true, AEX>(arp, aci, aval, X, row, lane, tpr, ldk, axh, axl);
   const size_t base = (size_t)row * ldk;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
 
 // YA = A X, YM = M X (X, YA, YM as float pairs) and per-block partial sums of
 // X .* YA, X .* YM (double-float per thread, float64 across the block).
-template <int CH>
+template <int CH, bool AEX>
 __global__ void __launch_bounds__(kBlock)
     k_border_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                 const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(kBlock)
     for (int v = 0; v < 2; ++v) sAh[c][v] = sAl[c][v] = sMh[c][v] = sMl[c][v] = 0.f;
   for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
     float yah[CH][2], yal[CH][2], ymh[CH][2], yml[CH][2];
-    gather_row_ff<CH, true>(arp, aci, aval, X, row, lane, tpr, ldk, yah, yal);
+    gather_row_ff<CH, true, AEX>(arp, aci, aval, X, row, lane, tpr, ldk, yah, yal);
     gather_row_ff<CH, true>(mrp, mci, mval, X, row, lane, tpr, ldk, ymh, yml);
     const size_t base = (size_t)row * ldk;
 #pragma unroll
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 // out = S X; FFIN / FFOUT: X / out as float pairs (else float64).
-template <int CH, bool FFIN, bool FFOUT>
+template <int CH, bool FFIN, bool FFOUT, bool EX>
 __global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const float2* __restrict__ av, const double* __restrict__ X,
                                                      double* __restrict__ out, int ldk, int tpr) {
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm_ff(int n, con
   const int lane = threadIdx.x % tpr;
   if (row >= n) return;
   float yh[CH][2], yl[CH][2];
-  gather_row_ff<CH, FFIN>(rp, ci, av, X, row, lane, tpr, ldk, yh, yl);
+  gather_row_ff<CH, FFIN, EX>(rp, ci, av, X, row, lane, tpr, ldk, yh, yl);
   const size_t base = (size_t)row * ldk;
 #pragma unroll
   for (int c = 0; c < CH; ++c) store_pair<FFOUT>(out, base + (c * tpr + lane) * 2, yh[c], yl[c]);
@@ -292,7 +296,7 @@ __global__ void k_from_ff(int64_t total, const double* __restrict__ in, double* 
 // pair array Usplit alone (the finest-level state of the mixed-precision step;
 // its float64 copy is made on demand), else U is written in float64 and, if
 // Usplit is given, also split into pairs.
-template <int CH, bool WFF>
+template <int CH, bool WFF, bool EX>
 __global__ void __launch_bounds__(kBlock)
     k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
                 const double* __restrict__ W, const double* __restrict__ X, const double* __restrict__ alpha,
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
     for (int c = 0; c < CH; ++c) load_pair<WFF>(W, base + (c * tpr + lane) * 2, wh[c], wl[c]);
   } else {
-    gather_row_ff<CH, WFF>(rp, ci, pv, W, row, lane, tpr, ldk, wh, wl);
+    gather_row_ff<CH, WFF, EX>(rp, ci, pv, W, row, lane, tpr, ldk, wh, wl);
   }
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
@@ -364,9 +368,12 @@ void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const 
     L.rows(A.n_rows);
     L.begin(KC_OUTER_RHS, nnz * 12.0 + 2 * (n + 1) * 4.0 + n * ldk * (16.0 + 4.0), 2.0 * nnz * ldk + 2.0 * n * ldk);
   }
-  PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH><<<grid, kBlock, 0, L.s>>>(
-                             A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, lam, U,
-                             reinterpret_cast<float2*>(Fd), R, ldk, g.tpr));
+#define PASM_FF_RHS(AEX)                                                                      \
+  PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH, AEX><<<grid, kBlock, 0, L.s>>>(                \
+                             A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, lam, U,            \
+                             reinterpret_cast<float2*>(Fd), R, ldk, g.tpr))
+  if (A.exact32) { PASM_FF_RHS(true); } else { PASM_FF_RHS(false); }
+#undef PASM_FF_RHS
   L.bump();
 }
 
@@ -379,8 +386,13 @@ void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const d
     L.rows(A.n_rows);
     L.begin(KC_OUTER_RES, nnz * 12.0 + (n + 1) * 4.0 + n * ldk * (16.0 + 4.0), 2.0 * nnz * ldk + n * ldk);
   }
-  PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH><<<grid, kBlock, 0, L.s>>>(
-                             A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+  if (A.exact32) {
+    PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH, true><<<grid, kBlock, 0, L.s>>>(
+                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+  } else {
+    PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH, false><<<grid, kBlock, 0, L.s>>>(
+                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+  }
   L.bump();
 }
 
@@ -399,8 +411,13 @@ int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const doub
     L.rows(A.n_rows);
     L.begin(KC_BORDER, nnz * 12.0 + 2 * (n + 1) * 4.0 + 3.0 * n * ldk * 8.0, 2.0 * nnz * ldk + 4.0 * n * ldk);
   }
-  PASM_FF_DISPATCH(g.ch, k_border_ff<CH><<<grid, kBlock, smem, L.s>>>(A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci,
-                                                                       M.vff, X, YA, YM, partials, ldk, g.tpr));
+  if (A.exact32) {
+    PASM_FF_DISPATCH(g.ch, k_border_ff<CH, true><<<grid, kBlock, smem, L.s>>>(
+                               A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, X, YA, YM, partials, ldk, g.tpr));
+  } else {
+    PASM_FF_DISPATCH(g.ch, k_border_ff<CH, false><<<grid, kBlock, smem, L.s>>>(
+                               A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, X, YA, YM, partials, ldk, g.tpr));
+  }
   L.bump();
   return grid;
 }
@@ -415,8 +432,14 @@ void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double*
     L.rows(S.n_rows);
     L.begin(KC_SPMM, nnz * 12.0 + (rows + 1) * 4.0 + cols * ldk * 8.0 + rows * ldk * 8.0, 2.0 * nnz * ldk);
   }
-#define PASM_FF_SPMM(FI, FO) \
-  PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, X, out, ldk, g.tpr))
+#define PASM_FF_SPMM(FI, FO)                                                                                   \
+  if (S.exact32) {                                                                                             \
+    PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO, true><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, X, \
+                                                                                  out, ldk, g.tpr));           \
+  } else {                                                                                                     \
+    PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO, false><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, \
+                                                                                   X, out, ldk, g.tpr));       \
+  }
   if (x_ff && out_ff) { PASM_FF_SPMM(true, true); }
   else if (x_ff) { PASM_FF_SPMM(true, false); }
   else if (out_ff) { PASM_FF_SPMM(false, true); }
@@ -461,13 +484,16 @@ void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, boo
   const int* rp = P ? P->rp : nullptr;
   const int* ci = P ? P->ci : nullptr;
   const float2* pv = P ? P->vff : nullptr;
+  const bool ex = P ? P->exact32 : true;
+#define PASM_FF_UPD(WF, EXV)                                                                                  \
+  PASM_FF_DISPATCH(g.ch, k_update_ff<CH, WF, EXV><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, \
+                                                                           Usplit, ldk, g.tpr, identity))
   if (w_ff) {
-    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, true><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, Usplit,
-                                                                            ldk, g.tpr, identity));
+    if (ex) { PASM_FF_UPD(true, true); } else { PASM_FF_UPD(true, false); }
   } else {
-    PASM_FF_DISPATCH(g.ch, k_update_ff<CH, false><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, Usplit,
-                                                                             ldk, g.tpr, identity));
+    if (ex) { PASM_FF_UPD(false, true); } else { PASM_FF_UPD(false, false); }
   }
+#undef PASM_FF_UPD
   L.bump();
 }
 

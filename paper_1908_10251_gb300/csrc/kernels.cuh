@@ -16,6 +16,7 @@ struct DCsr {
   double* v64 = nullptr;
   float* v32 = nullptr;
   float2* vff = nullptr;  // (hi, lo) float split of v64 for the double-float kernels (mixed precision)
+  bool exact32 = false;   // every value is a float32 (lo = 0): the double-float products drop that term
   // omega a_ij / a_jj (A only): the values of the second Jacobi sweep from a zero start
   double* w64 = nullptr;
   float* w32 = nullptr;

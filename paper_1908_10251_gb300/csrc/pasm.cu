@@ -192,9 +192,11 @@ int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32, bool spli
     // hi = nearest float, lo = nearest float of the remainder (about 48 bits)
     AL(c->allocs, &d.vff, (size_t)h.nnz);
     std::vector<float2> f((size_t)h.nnz);
+    d.exact32 = true;
     for (int64_t q = 0; q < h.nnz; ++q) {
       const float hi = (float)h.val[q];
       f[(size_t)q] = make_float2(hi, (float)(h.val[q] - (double)hi));
+      if (f[(size_t)q].y != 0.f) d.exact32 = false;
     }
     if (h.nnz) CK(cudaMemcpy(d.vff, f.data(), sizeof(float2) * (size_t)h.nnz, cudaMemcpyHostToDevice));
   }
