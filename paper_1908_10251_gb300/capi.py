@@ -42,7 +42,8 @@ class pasm_opts(ctypes.Structure):
     _fields_ = [("omega", ctypes.c_double), ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int),
                 ("cycles_per_step", ctypes.c_int), ("max_steps", ctypes.c_int), ("precision", ctypes.c_int),
                 ("score_norm", ctypes.c_int), ("init", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("smoother", ctypes.c_int), ("projection", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("projection", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("res_tol", ctypes.c_double)]
 
 
 class PasmError(RuntimeError):

@@ -629,6 +629,7 @@ void pasm_default_opts(pasm_opts* o) {
   o->smoother = PASM_JACOBI;
   o->projection = PASM_PROJ_TENSOR;
   o->autotune = 1;
+  o->res_tol = 0.0;
 }
 
 const char* pasm_strerror(int st) {
@@ -1101,9 +1102,34 @@ int pasm_solve(pasm_ctx* c, int k, double tol, const double* lambda0, const doub
   int r = pasm_init(c, k, tol, lambda0, U0);
   if (r) return r;
   int act = k;
+  std::vector<double> res;
+  std::vector<int> status, active;
   for (int s = 0; s < c->opts.max_steps && act > 0; ++s) {
+    const int before = act;
     r = pasm_step(c, &act);
     if (r) return r;
+    if (c->opts.res_tol > 0.0 && act < before) {
+      // pairs frozen by the |dlambda| test this step stay active unless their residual is small
+      res.assign((size_t)k, 0.0);
+      status.assign((size_t)k, 0);
+      active.assign((size_t)k, 0);
+      r = pasm_residuals(c, res.data());
+      if (r) return r;
+      CK(cudaMemcpy(status.data(), c->status, sizeof(int) * k, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(active.data(), c->active, sizeof(int) * k, cudaMemcpyDeviceToHost));
+      int back = 0;
+      for (int i = 0; i < k; ++i)
+        if (status[(size_t)i] == 1 && !(res[(size_t)i] <= c->opts.res_tol)) {
+          status[(size_t)i] = 0;
+          active[(size_t)i] = 1;
+          ++back;
+        }
+      if (back) {
+        CK(cudaMemcpy(c->status, status.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->active, active.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+        act += back;
+      }
+    }
   }
   r = pasm_get(c, lambda_out, U_out, steps_out, status_out);
   if (r) return r;

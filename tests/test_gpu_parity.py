@@ -194,6 +194,33 @@ def test_residual_report(pg, precision, tol):
     pg.pasm_destroy(ctx)
 
 
+def test_residual_guarded_freeze(pg):
+    """opts.res_tol: with a bound the converged pairs meet, pasm_solve ends as
+    without it (every pair converged, eigenvalues to 1e-10, residuals below the
+    bound); with a bound no pair can meet, no pair is reported converged and
+    pasm_solve returns PASM_ENOTCONV at max_steps."""
+    H = mg.build_hierarchy(2, 32, 8)
+    k = 5
+
+    def solve(**opts):
+        ctx = setup_ctx(pg, H, **opts)
+        lam = np.zeros(k); U = np.zeros((H.fine.n, k))
+        steps = np.zeros(k, dtype=np.int32); status = np.zeros(k, dtype=np.int32)
+        code = pg.pasm_solve(ctx, k, 1e-10, None, None, lam, U, steps, status)
+        res = pg.pasm_residuals(ctx)
+        pg.pasm_destroy(ctx)
+        return code, lam, status, res
+
+    code0, lam0, status0, _ = solve()
+    assert code0 == 0 and np.all(status0 == 1)
+    code1, lam1, status1, res1 = solve(res_tol=1e-6)
+    assert code1 == 0 and np.all(status1 == 1) and np.all(res1 <= 1e-6)
+    assert np.allclose(lam1, lam0, rtol=1e-10)
+    code2, lam2, status2, _ = solve(res_tol=1e-300, max_steps=12)
+    assert code2 == 5 and np.all(status2 == 0)
+    assert np.allclose(lam2, lam0, rtol=1e-9)
+
+
 def test_solve_converges_like_oracle(pg):
     """pasm_solve from the coarse initial pairs: the pairs the oracle converges
     (to the brute-force eigenvalues) converge on the GPU to the same values,
