@@ -126,3 +126,37 @@ def test_uneven_batch_full_size(pg):
     U = np.zeros((probs[1].fine.n, k))
     pg.pasm_solve(ctx, k, 1e-10, None, None, lam, U, None, None)
     assert np.array_equal(lam, lams[1]) and np.array_equal(U, Us[1])
+
+
+def test_residual_guard_rejects_spurious_freezes(pg):
+    """Problem 1 of the uneven batch (h = 1/512, kappa seed 1001, H = 1/16,
+    k = 16, mixed precision), where the |delta lambda| test alone reports pairs
+    converged at a value that is not an eigenvalue (residual about 4, see the
+    test above).  With opts.res_tol = 1e-3, every pair pasm_solve reports
+    converged has ||A u - lambda M u|| / (lambda ||u||_M) <= 1e-3, recomputed
+    in float64 on the CPU, and the run ends with PASM_ENOTCONV if any pair is
+    still iterating at max_steps."""
+    N, k = 512, 16
+    H = mg.build_hierarchy(2, N, 16, kappa=mg.gaussian_log_field(N, 1001))
+    A, M, P = parts(H)
+
+    def solve(res_tol):
+        opts = pg.pasm_default_opts(precision=1, max_steps=60, res_tol=res_tol)
+        ctx = pg.pasm_setup(A, M, P, opts, torch.cuda.current_stream().cuda_stream)
+        lam = np.zeros(k)
+        U = np.zeros((H.fine.n, k))
+        steps = np.zeros(k, dtype=np.int32)
+        status = np.zeros(k, dtype=np.int32)
+        code = pg.pasm_solve(ctx, k, 1e-10, None, None, lam, U, steps, status)
+        pg.pasm_destroy(ctx)
+        Af, Mf = H.fine.A, H.fine.M
+        MU = Mf @ U
+        res = np.linalg.norm(Af @ U - MU * lam[None, :], axis=0) / (lam * np.sqrt(np.einsum("ij,ij->j", U, MU)))
+        return code, status, res
+
+    _, status0, res0 = solve(0.0)
+    assert np.any((status0 == 1) & (res0 > 1e-3))           # the spurious freezes, unguarded
+    code, status, res = solve(1e-3)
+    conv = status == 1
+    assert np.all(res[conv] <= 1e-3 * (1 + 1e-6)), res[conv]
+    assert (code == 5) == bool(np.any(~conv))
