@@ -221,6 +221,32 @@ def test_residual_guarded_freeze(pg):
     assert np.allclose(lam2, lam0, rtol=1e-9)
 
 
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-11)])
+def test_pairs_independent_of_the_batch(pg, precision, tol):
+    """Pairs are independent (Section 3.2): three steps of k = 8 pairs in one
+    block give each pair what the same pair gives alone (k = 1, padded to a
+    block of 4), to rounding in the cross-row sums (pin P11)."""
+    H = mg.build_hierarchy(2, 64, 8)
+    prob = oracle.Problem.from_hierarchy(H)
+    k = 8
+    lam0, U0 = oracle.initial_state(prob, k)
+    ctx = setup_ctx(pg, H, precision=precision)
+    pg.pasm_init(ctx, k, 0.0, lam0, U0)
+    for _ in range(3):
+        pg.pasm_step(ctx)
+    lam, U, _, _ = get_state(pg, ctx, H.fine.n, k)
+    pg.pasm_destroy(ctx)
+    for i in (0, 3, 7):
+        c1 = setup_ctx(pg, H, precision=precision)
+        pg.pasm_init(c1, 1, 0.0, lam0[i:i + 1].copy(), np.ascontiguousarray(U0[:, i:i + 1]))
+        for _ in range(3):
+            pg.pasm_step(c1)
+        l1, U1, _, _ = get_state(pg, c1, H.fine.n, 1)
+        pg.pasm_destroy(c1)
+        assert abs(l1[0] / lam[i] - 1) <= tol, (i, l1[0], lam[i])
+        assert np.abs(U1[:, 0] - U[:, i]).max() / np.abs(U[:, i]).max() <= 100 * tol, i
+
+
 def test_solve_converges_like_oracle(pg):
     """pasm_solve from the coarse initial pairs: the pairs the oracle converges
     (to the brute-force eigenvalues) converge on the GPU to the same values,
