@@ -130,8 +130,9 @@ typedef struct {
                           4, 8) of every sparse kernel on every level with at
                           least 16384 rows and keep the fastest; 0: fixed
                           default shapes [1]                                     */
-  double res_tol;      /* > 0: in pasm_solve a pair that meets the |dlambda| test
-                          is kept iterating while its relative residual
+  double res_tol;      /* > 0: in pasm_solve and pasm_batch_solve a pair that
+                          meets the |dlambda| test is kept iterating while its
+                          relative residual
                           ||A u - lambda M u|| / (|lambda| ||u||_M) (the stopping
                           quantity of Section 5) exceeds res_tol, so a freeze on
                           a value that is not an eigenvalue is not reported as

@@ -11,6 +11,7 @@
 #include <vector>
 
 extern "C" int pasm_ctx_wait_active(pasm_ctx* c, int* n_active);
+extern "C" int pasm_ctx_guard_freezes(pasm_ctx* c, int* n_active);
 
 struct pasm_batch {
   std::vector<pasm_ctx*> ctx;
@@ -100,7 +101,8 @@ int pasm_batch_solve(pasm_batch* b, const int* k, double tol, double* const* lam
     for (int p = 0; p < np; ++p)
       if (b->active[(size_t)p] > 0) {
         int act = 0;
-        const int r = pasm_ctx_wait_active(b->ctx[(size_t)p], &act);
+        int r = pasm_ctx_wait_active(b->ctx[(size_t)p], &act);
+        if (!r && act < b->active[(size_t)p]) r = pasm_ctx_guard_freezes(b->ctx[(size_t)p], &act);
         if (r) return r;
         b->active[(size_t)p] = act;
         left += act > 0;

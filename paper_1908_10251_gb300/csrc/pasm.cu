@@ -1096,40 +1096,45 @@ int pasm_get(pasm_ctx* c, double* lambda, double* U, int* steps, int* status) {
   return perr ? PASM_ETIMEOUT : PASM_OK;
 }
 
+// The residual guard of opts.res_tol, after a step in which pairs froze: a pair
+// the |dlambda| test froze is made active again while its relative residual
+// exceeds the bound; *n_active counts it again.  No-op when res_tol <= 0.
+int pasm_ctx_guard_freezes(pasm_ctx* c, int* n_active) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  if (!(c->opts.res_tol > 0.0)) return PASM_OK;
+  const int k = c->k;
+  std::vector<double> res((size_t)k, 0.0);
+  std::vector<int> status((size_t)k, 0), active((size_t)k, 0);
+  int r = pasm_residuals(c, res.data());
+  if (r) return r;
+  CK(cudaMemcpy(status.data(), c->status, sizeof(int) * k, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(active.data(), c->active, sizeof(int) * k, cudaMemcpyDeviceToHost));
+  int back = 0;
+  for (int i = 0; i < k; ++i)
+    if (status[(size_t)i] == PASM_PAIR_CONVERGED && !(res[(size_t)i] <= c->opts.res_tol)) {
+      status[(size_t)i] = PASM_PAIR_ACTIVE;
+      active[(size_t)i] = 1;
+      ++back;
+    }
+  if (back) {
+    CK(cudaMemcpy(c->status, status.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->active, active.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+    if (n_active) *n_active += back;
+  }
+  return PASM_OK;
+}
+
 int pasm_solve(pasm_ctx* c, int k, double tol, const double* lambda0, const double* U0, double* lambda_out,
                double* U_out, int* steps_out, int* status_out) {
   if (!c) return PASM_EINVAL;
   int r = pasm_init(c, k, tol, lambda0, U0);
   if (r) return r;
   int act = k;
-  std::vector<double> res;
-  std::vector<int> status, active;
   for (int s = 0; s < c->opts.max_steps && act > 0; ++s) {
     const int before = act;
     r = pasm_step(c, &act);
+    if (!r && act < before) r = pasm_ctx_guard_freezes(c, &act);
     if (r) return r;
-    if (c->opts.res_tol > 0.0 && act < before) {
-      // pairs frozen by the |dlambda| test this step stay active unless their residual is small
-      res.assign((size_t)k, 0.0);
-      status.assign((size_t)k, 0);
-      active.assign((size_t)k, 0);
-      r = pasm_residuals(c, res.data());
-      if (r) return r;
-      CK(cudaMemcpy(status.data(), c->status, sizeof(int) * k, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(active.data(), c->active, sizeof(int) * k, cudaMemcpyDeviceToHost));
-      int back = 0;
-      for (int i = 0; i < k; ++i)
-        if (status[(size_t)i] == 1 && !(res[(size_t)i] <= c->opts.res_tol)) {
-          status[(size_t)i] = 0;
-          active[(size_t)i] = 1;
-          ++back;
-        }
-      if (back) {
-        CK(cudaMemcpy(c->status, status.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(c->active, active.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
-        act += back;
-      }
-    }
   }
   r = pasm_get(c, lambda_out, U_out, steps_out, status_out);
   if (r) return r;
