@@ -47,7 +47,7 @@ WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-10, "target": 1e-9,
           "stable_history": "cube_h128_H8_k32_nofreeze_history"}
 # the h = 1/2048 workload (4,190,209 DoF, H = 1/16, 8 grids, k = 128): its reference table holds the
 # 48 smallest eigenvalues, so only pairs 0..47 can be counted; no oracle history at this size
-WORK5 = {"dim": 2, "N": 2048, "NH": 16, "k": 128, "tol": 1e-10, "target": 1e-9,
+WORK_H2048 = {"dim": 2, "N": 2048, "NH": 16, "k": 128, "tol": 1e-10, "target": 1e-9,
          "golden": "square_h2048_k48", "history": None}
 METRIC = "eigenpairs/s to 1e-9 rel. eigenvalue error"
 FP64_PEAK_TFLOPS = 1.259   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (measured 1.198)
@@ -441,12 +441,12 @@ def main_ours(args):
                                                  args.calib_steps, work=WORK3D)
         del H3
     # the h = 1/2048, k = 128 workload (when its reference table is present)
-    H5 = None
-    if not args.no_c5 and os.path.exists(os.path.join(ROOT, "tests", "golden", WORK5["golden"] + ".txt")):
-        H5 = mg.build_hierarchy(WORK5["dim"], WORK5["N"], WORK5["NH"])
-        ref5 = load_golden(WORK5["golden"])
-        res["square_h2048_H16_k128_mixed"] = run_mode(pg, torch, H5, ref5, 1, args.steps, args.warmup, rank,
-                                                      args.calib_steps, work=WORK5)
+    H2048 = None
+    if not args.no_h2048 and os.path.exists(os.path.join(ROOT, "tests", "golden", WORK_H2048["golden"] + ".txt")):
+        H2048 = mg.build_hierarchy(WORK_H2048["dim"], WORK_H2048["N"], WORK_H2048["NH"])
+        ref2048 = load_golden(WORK_H2048["golden"])
+        res["square_h2048_H16_k128_mixed"] = run_mode(pg, torch, H2048, ref2048, 1, args.steps, args.warmup, rank,
+                                                      args.calib_steps, work=WORK_H2048)
     training = None
     if args.learned:
         w, train_s, losses = train_smoother(pg, torch, H)
@@ -457,15 +457,15 @@ def main_ours(args):
         coarse[-2:] = 0
         res["mixed_learned_coarse"] = run_mode(pg, torch, H, ref, 1, args.steps, args.warmup, rank,
                                                args.calib_steps, nn_weights=w, nn_widths=coarse)
-        if H5 is not None:
+        if H2048 is not None:
             # the same network (the 2D stencil is h-independent) on the h = 1/2048 workload
-            coarse5 = grid_widths(H5)
-            coarse5[-2:] = 0
+            coarse2048 = grid_widths(H2048)
+            coarse2048[-2:] = 0
             res["square_h2048_H16_k128_learned_coarse"] = run_mode(
-                pg, torch, H5, load_golden(WORK5["golden"]), 1, args.steps, args.warmup, rank, args.calib_steps,
-                nn_weights=w, nn_widths=coarse5, work=WORK5)
+                pg, torch, H2048, load_golden(WORK_H2048["golden"]), 1, args.steps, args.warmup, rank, args.calib_steps,
+                nn_weights=w, nn_widths=coarse2048, work=WORK_H2048)
         training = {"seconds": train_s, "loss_first": losses[0], "loss_last": losses[-1]}
-    H5 = None
+    H2048 = None
     primary, primary_prec = modes[0]
     main = res[primary]
     S, conv, ms_step = main["S"], main["converged"], main["ms_per_step"]
@@ -628,7 +628,7 @@ def main():
                     help="also train the learned post-smoother and run the mixed mode with it (default)")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-3d", dest="no_3d", action="store_true", help="skip the 3D workload variant")
-    ap.add_argument("--no-c5", dest="no_c5", action="store_true", help="skip the h = 1/2048, k = 128 variant")
+    ap.add_argument("--no-h2048", dest="no_h2048", action="store_true", help="skip the h = 1/2048, k = 128 variant")
     args = ap.parse_args()
     if args.impl == "reference":
         main_reference(args)

@@ -225,7 +225,7 @@ def test_residual_guarded_freeze(pg):
 def test_pairs_independent_of_the_batch(pg, precision, tol):
     """Pairs are independent (Section 3.2): three steps of k = 8 pairs in one
     block give each pair what the same pair gives alone (k = 1, padded to a
-    block of 4), to rounding in the cross-row sums (pin P11)."""
+    block of 4), to rounding in the cross-row sums."""
     H = mg.build_hierarchy(2, 64, 8)
     prob = oracle.Problem.from_hierarchy(H)
     k = 8
