@@ -4,11 +4,13 @@
 // Section 3.1), the transfer chains and the update.  Vectors that are gathered
 // through a sparse matrix are kept as (hi, lo) float pairs ("ff", 8 bytes per
 // entry like float64): the multigrid iterate u~, its products A u~ and M u~,
-// the intermediate levels of the transfer chains, and a per-step split copy of
-// U.  Matrix values are split once at setup.  The state U, the coarse vectors
-// and the eigenvalues stay float64.  Results carry about 2^-46 relative to the
-// sum of the magnitudes of their terms (float64: 2^-53), far below what the
-// float32 V-cycles of the mixed path resolve.
+// the intermediate levels of the transfer chains, and the state U itself
+// between steps (its float64 form is rebuilt when read).  Matrix values are
+// split once at setup; a matrix whose values are all float32 skips the
+// low-part products.  The coarse vectors and the eigenvalues stay float64.
+// Results carry about 2^-46 relative to the sum of the magnitudes of their
+// terms (float64: 2^-53), far below what the float32 V-cycles of the mixed
+// path resolve.
 #include "common.cuh"
 #include "ff.cuh"
 #include "kernels.cuh"
