@@ -181,9 +181,10 @@ void axpy_ff(const Launch& L, int n, const double* B, bool b_ff, const float* E,
 // Conversions of total entries: float64 -> pairs (may be in place), pairs -> float64.
 void to_ff(const Launch& L, int64_t total, const double* in, double* out);
 void from_ff(const Launch& L, int64_t total, const double* in, double* out);
-// U = alpha X + P W for updated pairs (float64 U, X in pairs, W in pairs if
-// w_ff); P == nullptr means P = identity on n rows.  Usplit (optional)
-// receives U as pairs.
+// U = alpha X + P W for updated pairs (X in pairs, W in pairs if w_ff); P ==
+// nullptr means P = identity on n rows.  With U given, U is float64 and Usplit
+// (optional) receives it as pairs; with U null the result goes to Usplit alone
+// (the pair state).  Frozen pairs are not touched.
 void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
                      const double* alpha, const int* upd, double* U, double* Usplit, int ldk);
 
