@@ -429,3 +429,17 @@ def test_cg_smoothed_pasm_matches_brute_force():
     lam, U, steps, _ = op.solve(prob, 5, tol=1e-12, max_steps=60, history=True)
     dense = sla.eigh(H.fine.A.toarray(), H.fine.M.toarray(), eigvals_only=True, subset_by_index=[0, 4])
     assert np.abs(lam - dense).max() / dense.max() < 1e-10
+
+
+@pytest.mark.parametrize("dim,Nf,Nc,count", [(2, 64, 16, 12), (3, 16, 8, 10)])
+def test_lobpcg_reference_matches_shift_invert(dim, Nf, Nc, count):
+    """The LOBPCG reference (used for the meshes too large to factorise: the 3D
+    cube at h = 1/128 and the square at h = 1/2048) against ARPACK shift-invert
+    on meshes small enough for both: the same smallest eigenvalues to 1e-9,
+    with a small residual."""
+    from oracle.reference import smallest_eigenvalues, smallest_eigenvalues_lobpcg
+    H = mg.build_hierarchy(dim, Nf, Nc)
+    vals, res = smallest_eigenvalues_lobpcg(H, count, tol=1e-9)
+    ref = smallest_eigenvalues(H.fine.A, H.fine.M, count)
+    assert res < 1e-6
+    assert np.allclose(vals, ref, rtol=1e-9), np.abs(vals / ref - 1).max()
