@@ -27,6 +27,17 @@ def test_clusters_and_first_reach():
     assert list(reach) == [1, 1, 2, -1]
 
 
+def test_first_reach_with_a_shorter_reference_table():
+    """More pairs than reference eigenvalues (the h = 1/2048, k = 128 workload
+    has a 48-value table): pairs past the table never count, the rest do."""
+    ref = np.array([1.0, 2.0, 3.0])
+    hist = np.array([[1.0, 2.0, 3.0, 4.0, 5.0]])
+    assert list(bench.first_reach(hist, ref, 1e-9, ref)) == [0, 0, 0, -1, -1]
+    assert bench.reference_set(bench.WORK_H2048) is None
+    conv, S = bench.time_to_target(np.array([0, 3, -1, -1]), None, 60)
+    assert (conv, S) == (2, 3)
+
+
 def test_time_to_target_with_and_without_reference_set():
     reach = np.array([3, 5, -1, 7])
     assert bench.time_to_target(reach, None, 60) == (3, 7)
