@@ -33,6 +33,18 @@ def test_default_opts(capi):
     assert o.precision == capi.PASM_FP64 and o.score_norm == capi.PASM_SCORE_A
 
 
+def test_opts_layout_matches_the_header(capi):
+    """pasm_default_opts writes exactly the binding's pasm_opts: bytes past it
+    stay untouched, and every field after the integer block, the trailing
+    float64 res_tol included, has its documented default."""
+    size = ctypes.sizeof(capi.pasm_opts)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    capi.load_library().pasm_default_opts(ctypes.cast(buf, ctypes.POINTER(capi.pasm_opts)))
+    assert all(b == 0xAB for b in bytes(buf)[size:])
+    o = capi.pasm_opts.from_buffer_copy(bytes(buf)[:size])
+    assert o.autotune == 1 and o.res_tol == 0.0 and abs(o.omega - 2.0 / 3.0) < 1e-15
+
+
 def test_strerror(capi):
     assert capi.pasm_strerror(0) == "success"
     assert "coarse" in capi.pasm_strerror(capi.PASM_EK_TOO_BIG)
