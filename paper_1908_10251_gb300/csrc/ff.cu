@@ -119,6 +119,68 @@ __device__ __forceinline__ void gather_row_ff(const int* __restrict__ rp, const 
   }
 }
 
+// A X and M X together over M's pattern (am: A's and M's split values per
+// entry, a = 0 where A has no entry): one gather of each row of X serves both
+// products.  Each accumulator sees the same terms in the same order as the
+// separate gathers (A's entries in M's column order).
+template <int CH, int N, bool FFIN, bool AEX>
+__device__ __forceinline__ void gather_group_am(const int* __restrict__ ci, const float4* __restrict__ am,
+                                                const double* __restrict__ X, int p, int lane, int tpr, int ldk,
+                                                float (&ah)[CH][2], float (&al)[CH][2], float (&mh)[CH][2],
+                                                float (&ml)[CH][2]) {
+  int j[N];
+  float4 w[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    j[u] = __ldg(ci + p + u);
+    w[u] = __ldg(am + p + u);
+  }
+  float xh[N][CH][2], xl[N][CH][2];
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) load_pair<FFIN>(X, (size_t)j[u] * ldk + (c * tpr + lane) * 2, xh[u][c], xl[u][c]);
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    const bool has_a = w[u].x != 0.f;
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        ff_mac(mh[c][v], ml[c][v], w[u].z, w[u].w, xh[u][c][v], xl[u][c][v]);
+        if (has_a) {
+          if (AEX) ff_mac_exact(ah[c][v], al[c][v], w[u].x, xh[u][c][v], xl[u][c][v]);
+          else ff_mac(ah[c][v], al[c][v], w[u].x, w[u].y, xh[u][c][v], xl[u][c][v]);
+        }
+      }
+  }
+}
+
+template <int CH, bool FFIN, bool AEX>
+__device__ __forceinline__ void gather_row_am(const int* __restrict__ rp, const int* __restrict__ ci,
+                                              const float4* __restrict__ am, const double* __restrict__ X, int row,
+                                              int lane, int tpr, int ldk, float (&ah)[CH][2], float (&al)[CH][2],
+                                              float (&mh)[CH][2], float (&ml)[CH][2]) {
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) ah[c][v] = al[c][v] = mh[c][v] = ml[c][v] = 0.f;
+  int p = __ldg(rp + row);
+  const int p1 = __ldg(rp + row + 1);
+  for (; p + 4 <= p1; p += 4) gather_group_am<CH, 4, FFIN, AEX>(ci, am, X, p, lane, tpr, ldk, ah, al, mh, ml);
+  const int rem = p1 - p;
+  if (rem == 3) gather_group_am<CH, 3, FFIN, AEX>(ci, am, X, p, lane, tpr, ldk, ah, al, mh, ml);
+  else if (rem == 2) gather_group_am<CH, 2, FFIN, AEX>(ci, am, X, p, lane, tpr, ldk, ah, al, mh, ml);
+  else if (rem == 1) gather_group_am<CH, 1, FFIN, AEX>(ci, am, X, p, lane, tpr, ldk, ah, al, mh, ml);
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      ff_norm(ah[c][v], al[c][v]);
+      ff_norm(mh[c][v], ml[c][v]);
+    }
+}
+
 // Store two entries as float pairs or, rounded, as float64.
 template <bool FF>
 __device__ __forceinline__ void store_pair(double* __restrict__ out, size_t off, const float (&h)[2],
@@ -140,6 +202,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
   const int lane = threadIdx.x % tpr;
   if (row >= n) return;
   float muh[CH][2], mul[CH][2], auh[CH][2], aul[CH][2];
+  // two separate gathers: the one-gather form (as in the bordering kernel) needs more registers
+  // than the four blocks per SM this kernel runs at, and was slower (0.57 -> 0.63 ms)
   gather_row_ff<CH, true>(mrp, mci, mval, U, row, lane, tpr, ldk, muh, mul);
   gather_row_ff<CH, true, AEX>(arp, aci, aval, U, row, lane, tpr, ldk, auh, aul);
   const size_t base = (size_t)row * ldk;
@@ -184,12 +248,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
 
 // YA = A X, YM = M X (X, YA, YM as float pairs) and per-block partial sums of
 // X .* YA, X .* YM (double-float per thread, float64 across the block).
-template <int CH, bool AEX>
+template <int CH, bool AEX, bool MERGED>
 __global__ void __launch_bounds__(kBlock)
     k_border_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                 const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
                 const double* __restrict__ X, double* __restrict__ YA, double* __restrict__ YM,
-                double* __restrict__ partials, int ldk, int tpr) {
+                double* __restrict__ partials, int ldk, int tpr, const float4* __restrict__ am) {
   extern __shared__ double red[];  // [rpb][2][ldk]
   const int rpb = kBlock / tpr;
   const int grp = threadIdx.x / tpr;
@@ -201,8 +265,12 @@ __global__ void __launch_bounds__(kBlock)
     for (int v = 0; v < 2; ++v) sAh[c][v] = sAl[c][v] = sMh[c][v] = sMl[c][v] = 0.f;
   for (int row = blockIdx.x * rpb + grp; row < n; row += gridDim.x * rpb) {
     float yah[CH][2], yal[CH][2], ymh[CH][2], yml[CH][2];
-    gather_row_ff<CH, true, AEX>(arp, aci, aval, X, row, lane, tpr, ldk, yah, yal);
-    gather_row_ff<CH, true>(mrp, mci, mval, X, row, lane, tpr, ldk, ymh, yml);
+    if (MERGED) {
+      gather_row_am<CH, true, AEX>(mrp, mci, am, X, row, lane, tpr, ldk, yah, yal, ymh, yml);
+    } else {
+      gather_row_ff<CH, true, AEX>(arp, aci, aval, X, row, lane, tpr, ldk, yah, yal);
+      gather_row_ff<CH, true>(mrp, mci, mval, X, row, lane, tpr, ldk, ymh, yml);
+    }
     const size_t base = (size_t)row * ldk;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -413,13 +481,15 @@ int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const doub
     L.rows(A.n_rows);
     L.begin(KC_BORDER, nnz * 12.0 + 2 * (n + 1) * 4.0 + 3.0 * n * ldk * 8.0, 2.0 * nnz * ldk + 4.0 * n * ldk);
   }
-  if (A.exact32) {
-    PASM_FF_DISPATCH(g.ch, k_border_ff<CH, true><<<grid, kBlock, smem, L.s>>>(
-                               A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, X, YA, YM, partials, ldk, g.tpr));
+#define PASM_FF_BORDER(AEX, MG)                                                                \
+  PASM_FF_DISPATCH(g.ch, k_border_ff<CH, AEX, MG><<<grid, kBlock, smem, L.s>>>(                 \
+                             A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, X, YA, YM, partials, ldk, g.tpr, M.am))
+  if (M.am) {
+    if (A.exact32) { PASM_FF_BORDER(true, true); } else { PASM_FF_BORDER(false, true); }
   } else {
-    PASM_FF_DISPATCH(g.ch, k_border_ff<CH, false><<<grid, kBlock, smem, L.s>>>(
-                               A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, X, YA, YM, partials, ldk, g.tpr));
+    if (A.exact32) { PASM_FF_BORDER(true, false); } else { PASM_FF_BORDER(false, false); }
   }
+#undef PASM_FF_BORDER
   L.bump();
   return grid;
 }

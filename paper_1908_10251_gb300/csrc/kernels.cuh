@@ -17,6 +17,9 @@ struct DCsr {
   float* v32 = nullptr;
   float2* vff = nullptr;  // (hi, lo) float split of v64 for the double-float kernels (mixed precision)
   bool exact32 = false;   // every value is a float32 (lo = 0): the double-float products drop that term
+  // (M of a level only) on M's pattern, A's split value beside M's: (a hi, a lo, m hi, m lo), a = 0
+  // where A has no entry; present when A's pattern lies inside M's, for one gather of both products
+  float4* am = nullptr;
   // omega a_ij / a_jj (A only): the values of the second Jacobi sweep from a zero start
   double* w64 = nullptr;
   float* w32 = nullptr;

@@ -694,6 +694,34 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
     int r = upload_csr(c, A[l], v.A, mixed, mixed);
     if (!r) r = upload_csr(c, M[l], v.M, false, mixed);
     if (r) return r;
+    if (mixed && l >= 1) {
+      // A's and M's split values together on M's pattern, for the kernels that gather the same
+      // vector through both (f = lam M u with r = f - A u; A u~ and M u~): one gather serves both.
+      // Used when every row of A matches a subsequence of the same row of M (column order kept).
+      const pasm_csr& a = A[l];
+      const pasm_csr& m = M[l];
+      std::vector<float4> am((size_t)m.nnz);
+      bool ok = true;
+      for (int i = 0; i < v.n && ok; ++i) {
+        int q = a.row_ptr[i];
+        const int qe = a.row_ptr[i + 1];
+        for (int p2 = m.row_ptr[i]; p2 < m.row_ptr[i + 1]; ++p2) {
+          const float mh = (float)m.val[p2];
+          float ah = 0.f, al = 0.f;
+          if (q < qe && a.col[q] == m.col[p2]) {
+            ah = (float)a.val[q];
+            al = (float)(a.val[q] - (double)ah);
+            ++q;
+          }
+          am[(size_t)p2] = make_float4(ah, al, mh, (float)(m.val[p2] - (double)mh));
+        }
+        if (q != qe) ok = false;
+      }
+      if (ok && m.nnz > 0) {
+        AL(c->allocs, &v.M.am, (size_t)m.nnz);
+        CK(cudaMemcpy(v.M.am, am.data(), sizeof(float4) * (size_t)m.nnz, cudaMemcpyHostToDevice));
+      }
+    }
     std::vector<double> d((size_t)v.n, 0.0);
     for (int i = 0; i < v.n; ++i)
       for (int q = A[l].row_ptr[i]; q < A[l].row_ptr[i + 1]; ++q)
