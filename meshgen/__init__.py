@@ -317,13 +317,11 @@ def build_hierarchy(dim: int, N_fine: int, N_coarse: int, kappa=None, galerkin: 
     return Hierarchy(levels, Ps)
 
 
-def gaussian_log_field(N: int, seed: int, sigma: float = 1.0, corr: float = 0.1) -> np.ndarray:
-    """Seeded stationary Gaussian field g on the (N+1)^2 nodes of the unit square.
-
-    Squared-exponential covariance sigma^2 exp(-d^2 / (2 corr^2)), synthesised
-    spectrally on a periodic (2N)^2 grid of spacing 1/N and cropped.  Returns
-    the per-triangle coefficient kappa = exp(mean of g over the triangle's
-    vertices) in the layout `assemble` expects: shape (2, N, N)."""
+def gaussian_field_nodes(N: int, seed: int, sigma: float = 1.0, corr: float = 0.1) -> np.ndarray:
+    """Seeded stationary Gaussian field g on the (N+1)^2 nodes of the unit square
+    (node (i, j) at (i/N, j/N)): squared-exponential covariance
+    sigma^2 exp(-d^2 / (2 corr^2)), synthesised spectrally on a periodic (2N)^2
+    grid of spacing 1/N and cropped."""
     rng = np.random.default_rng(seed)
     L = 2 * N
     k = np.fft.fftfreq(L, d=1.0 / N) * 2 * np.pi          # angular wavenumbers
@@ -333,7 +331,15 @@ def gaussian_log_field(N: int, seed: int, sigma: float = 1.0, corr: float = 0.1)
     dA = (2 * np.pi * N / L) ** 2
     noise = rng.standard_normal((L, L)) + 1j * rng.standard_normal((L, L))
     g = np.fft.ifft2(noise * np.sqrt(S * dA / (2 * np.pi) ** 2)) * L * L
-    g = np.real(g)[: N + 1, : N + 1]
+    return np.real(g)[: N + 1, : N + 1]
+
+
+def gaussian_log_field(N: int, seed: int, sigma: float = 1.0, corr: float = 0.1) -> np.ndarray:
+    """The coefficient kappa = exp(g) of the variable-coefficient problems, g
+    the field of `gaussian_field_nodes`: per triangle, kappa = exp(mean of g
+    over the triangle's vertices), in the layout `assemble` expects: shape
+    (2, N, N)."""
+    g = gaussian_field_nodes(N, seed, sigma, corr)
     simp = reference_simplices(2)
     kap = np.empty((2, N, N))
     for t, offs in enumerate(simp):
