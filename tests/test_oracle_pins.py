@@ -156,18 +156,119 @@ def test_coarse_correction_is_a_orthogonal_projection():
     assert np.abs(r).max() <= 1e-12 * np.abs(H.P[0].T @ f).max()
 
 
-def test_bvp_solve_is_two_vcycles_from_u():
-    """Algorithm 1 step 1 with the readings stated in the oracle: the right-hand
-    side is lambda M u and the multigrid iteration starts from u; two cycles
-    equal two applications of one cycle."""
+def _grid_modes(dim, N, modes):
+    """Sine modes prod_d sin(m_d pi x_d) on the interior nodes of the uniform
+    grid (x fastest), one column per mode."""
+    t = np.arange(1, N) / N
+    cols = []
+    for m in modes:
+        v = np.ones(1)
+        for d in range(dim):             # the last axis varies slowest
+            v = np.kron(np.sin(m[d] * np.pi * t), v) if d else np.sin(m[0] * np.pi * t)
+        cols.append(v)
+    return np.column_stack(cols)
+
+
+@pytest.mark.parametrize("dim,N,omega,nu", [(2, 16, 2.0 / 3.0, 1), (2, 16, 2.0 / 3.0, 2), (2, 32, 1.0, 3),
+                                            (3, 8, 2.0 / 3.0, 2), (3, 8, 0.8, 1)])
+def test_jacobi_damping_factor_closed_form(dim, N, omega, nu):
+    """Damped Jacobi on the P1 stiffness (5-point stencil (4, -1) in 2D; h times
+    the 7-point stencil (6, -1) on the Kuhn mesh in 3D): the grid sine modes
+    are eigenvectors of D^{-1} A with eigenvalue 1 - mean_d cos(m_d pi h), so
+    nu sweeps with f = 0 multiply a mode by
+    (1 - omega (1 - mean_d cos(m_d pi h)))^nu  (the textbook local Fourier
+    factor).  Checked through the oracle's level smoother on every level of a
+    hierarchy, so a wrong omega, a wrong level's D^{-1} (the 3D diagonal
+    halves per refinement) or a sweep count off by one all fail."""
+    Nc = 4 if dim == 2 else 2
+    H = mg.build_hierarchy(dim, N, Nc)
+    prob = oracle.Problem.from_hierarchy(H, omega=omega)
+    rng = np.random.default_rng(nu)
+    for l, lv in enumerate(H.levels):
+        if lv.N < 4:
+            continue
+        modes = [tuple(int(v) for v in rng.integers(1, lv.N, size=dim)) for _ in range(4)]
+        modes.append((1,) * dim)
+        modes.append((lv.N - 1,) * dim)
+        X = _grid_modes(dim, lv.N, modes)
+        Y = op.smooth(prob, l, np.zeros_like(X), X.copy(), nu)
+        for j, m in enumerate(modes):
+            mu = np.mean([np.cos(mm * np.pi / lv.N) for mm in m])
+            sig = (1.0 - omega * (1.0 - mu)) ** nu
+            assert np.abs(Y[:, j] - sig * X[:, j]).max() <= 1e-13, (l, m, sig)
+
+
+def _sine_smoother(N, omega, nu):
+    """nu damped-Jacobi sweeps (f = 0) on the 2D 5-point stencil, applied in the
+    sine basis: type-I discrete sine transform, multiply mode (m, n) by
+    (1 - omega (1 - (cos m pi h + cos n pi h) / 2))^nu, transform back.  An
+    implementation of the smoother that shares nothing with a sweep loop."""
+    import scipy.fft as sfft
+    c = np.cos(np.arange(1, N) * np.pi / N)
+    sig = (1.0 - omega * (1.0 - 0.5 * (c[:, None] + c[None, :]))) ** nu
+
+    def apply(e):
+        g = e.reshape(N - 1, N - 1, -1)
+        return sfft.idstn(sig[:, :, None] * sfft.dstn(g, type=1, axes=(0, 1)), type=1, axes=(0, 1)).reshape(e.shape)
+    return apply
+
+
+def _vcycle_error_operator(H, l, omega, nu1, nu2):
+    """Error propagation of the V-cycle on level l of a 2D hierarchy, from its
+    definition as an iteration: E_0 = 0 (exact coarsest solve) and
+    E_l = S^nu2 (I - P (I - E_{l-1}) A_{l-1}^{-1} P^T A_l) S^nu1, the inner
+    cycle started from zero.  Smoothers in the sine basis, coarse solves
+    dense.  Returns a function e -> E_l e."""
+    if l == 0:
+        return lambda e: np.zeros_like(e)
+    N = H.levels[l].N
+    S1, S2 = _sine_smoother(N, omega, nu1), _sine_smoother(N, omega, nu2)
+    A, P = H.levels[l].A, H.P[l - 1]
+    Ac = H.levels[l - 1].A.toarray()
+    Ec = _vcycle_error_operator(H, l - 1, omega, nu1, nu2)
+
+    def apply(e):
+        e1 = S1(e)
+        y = np.linalg.solve(Ac, P.T @ (A @ e1))
+        return S2(e1 - P @ (y - Ec(y)))
+    return apply
+
+
+@pytest.mark.parametrize("Nf,Nc,nu1,nu2", [(16, 8, 2, 2), (32, 4, 2, 2), (32, 4, 1, 3), (16, 4, 3, 0)])
+def test_vcycle_error_propagation(Nf, Nc, nu1, nu2):
+    """One V-cycle on A x = f started from x* + e (x* = A^{-1} f) leaves the
+    error E e, with E the cycle's error-propagation operator built from the
+    definition of multigrid (smoothing in the sine basis, the coarse problem
+    solved by the level below from zero, exact on V_H).  Pins the pre/post
+    sweep counts and their order, omega, P versus P^T, and the recursion."""
+    H = mg.build_hierarchy(2, Nf, Nc)
+    prob = oracle.Problem.from_hierarchy(H, nu_pre=nu1, nu_post=nu2)
+    rng = np.random.default_rng(Nf + Nc + nu1)
+    n = H.fine.n
+    xs = rng.standard_normal((n, 2))
+    f = H.fine.A @ xs
+    e = rng.standard_normal((n, 2))
+    x1 = op.vcycle(prob, prob.L, f, xs + e)
+    E = _vcycle_error_operator(H, prob.L, 2.0 / 3.0, nu1, nu2)
+    assert np.abs((x1 - xs) - E(e)).max() <= 1e-11 * np.abs(e).max()
+
+
+def test_bvp_solve_error_is_cycles_of_error_operator():
+    """Algorithm 1 step 1 with the readings stated in the oracle: the boundary
+    value problem A u^ = lambda M u (right-hand side lambda b(u, .)) solved by
+    `cycles` V-cycles from u, so u~ - u^ = E^cycles (u - u^), with u^ from a
+    direct solve and E the error operator of the test above."""
     H = mg.build_hierarchy(2, 16, 4)
-    prob = oracle.Problem.from_hierarchy(H)
-    lam, U = oracle.initial_state(prob, 2)
-    Ut = op.bvp_solve(prob, lam, U)
-    f = (H.fine.M @ U) * lam
-    x = op.vcycle(prob, prob.L, f, U.copy())
-    x = op.vcycle(prob, prob.L, f, x)
-    assert np.array_equal(x, Ut)
+    for cycles in (1, 2, 3):
+        prob = oracle.Problem.from_hierarchy(H, cycles=cycles)
+        lam, U = oracle.initial_state(prob, 3)
+        Ut = op.bvp_solve(prob, lam, U)
+        Uhat = spla.spsolve(H.fine.A.tocsc(), (H.fine.M @ U) * lam)
+        E = _vcycle_error_operator(H, prob.L, 2.0 / 3.0, 2, 2)
+        e = U - Uhat
+        for _ in range(cycles):
+            e = E(e)
+        assert np.abs((Ut - Uhat) - e).max() <= 1e-12 * np.abs(U).max(), cycles
 
 
 # ----------------------------------------------------------------------------- Algorithm 1 step 2

@@ -115,3 +115,54 @@ def test_bf16_rounding_matches_torch():
     x = np.random.default_rng(9).standard_normal(1000) * 10.0 ** np.random.default_rng(10).integers(-5, 5, 1000)
     ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(sm.bf16(x), ref)
+
+
+def torch_forward_bf16(w, R, nx, ny):
+    """N(r) with the second convolution taking bfloat16 operands: torch rounds
+    relu(+-z1) and W2 (via float32, round to nearest even), conv2d multiplies
+    the rounded values exactly in float64; layers 1 and 3 stay float64."""
+    W1, W2, W3 = sm.unpack(w)
+    F = torch.nn.functional
+
+    def tw(W):
+        return torch.tensor(np.transpose(W, (3, 2, 0, 1)))
+
+    def rb(t):
+        return t.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+    x = torch.tensor(np.asarray(R).T.reshape(-1, 1, ny, nx))
+    z1 = F.conv2d(x, tw(W1), padding=1)
+    W2b = rb(tw(W2))
+    z2p = F.conv2d(rb(F.relu(z1)), W2b, padding=1)
+    z2m = F.conv2d(rb(F.relu(-z1)), W2b, padding=1)
+    h = 0.5 * (F.relu(z2p) - F.relu(z2m))
+    return F.conv2d(h, tw(W3), padding=1)
+
+
+def test_bf16_layer2_branch_matches_torch():
+    """The tensor-core form of the network (layer 2 on bfloat16 operands,
+    products exact and summed in high precision) against torch's rounding and
+    conv2d of the same operands."""
+    A, R, w, nx, ny = small_case(3, N=12, k=3)
+    ours = sm.apply(w, sm.to_grid(R, nx, ny), bf16_layer2=True)
+    ref = torch_forward_bf16(w, R, nx, ny).numpy()[:, 0]
+    assert np.allclose(ours, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # the rounding is really applied: the plain network differs
+    plain = sm.apply(w, sm.to_grid(R, nx, ny))
+    assert np.abs(plain - ours).max() > 1e-6 * np.abs(plain).max()
+
+
+def test_bf16_layer2_exact_when_operands_representable():
+    """With weights and inputs on a coarse dyadic grid every operand of layer 2
+    is already a bfloat16 number (small integers times powers of two), so the
+    rounding is the identity and the bf16 form equals the float64 network
+    exactly; odd symmetry N(-r) = -N(r) holds in both forms."""
+    rng = np.random.default_rng(4)
+    ws = [rng.integers(-3, 4, size=s).astype(np.float64) * 0.25 for s in sm.SHAPES]
+    w = sm.pack(ws)
+    nx = ny = 9
+    r = rng.integers(-4, 5, size=(2, ny, nx)).astype(np.float64)
+    a = sm.apply(w, r, bf16_layer2=True)
+    b = sm.apply(w, r)
+    assert np.array_equal(a, b)
+    assert np.array_equal(sm.apply(w, -r, bf16_layer2=True), -a)
