@@ -363,9 +363,11 @@ int pasm_nn_errors(pasm_ctx* ctx, int* count);
  * since each call writes every entry it later reads.  All calls share that
  * array, so calls whose kernels may overlap on the GPU (different streams,
  * or concurrent host threads) race; serialise them.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call outside any stream capture.  Errors: PASM_EINVAL (sizes or
- * NULL pointers), PASM_ECUDA. */
+ * device looks up the array's device address (cudaGetSymbolAddress) and
+ * caches it for the life of the process; make that first call outside any
+ * stream capture.  A cudaDeviceReset invalidates the cached address: do not
+ * call this entry point on a device after resetting it.  Errors: PASM_EINVAL
+ * (sizes or NULL pointers), PASM_ECUDA. */
 int pasm_border_noalloc(int n, const int32_t* A_row_ptr, const int32_t* A_col, const double* A_val,
                         int64_t A_nnz, const int32_t* M_row_ptr, const int32_t* M_col, const double* M_val,
                         int64_t M_nnz, int k, const double* X, double* YA, double* YM, double* beta,
@@ -373,8 +375,11 @@ int pasm_border_noalloc(int n, const int32_t* A_row_ptr, const int32_t* A_col, c
 
 /* ---- Batches of independent problems of uneven size (several meshes, several
  * k per mesh).  Distinct problems, like the pairs of Algorithm 2, never
- * exchange data; the batch steps them together, each on its own stream, so
- * that the correction steps of small problems overlap on the GPU. */
+ * exchange data (Section 3.2, the remark after Algorithm 2 on distributing
+ * eigenpairs over processes); the batch steps them together: one batch step is
+ * one replay of one captured CUDA graph holding the correction step of every
+ * unfinished problem on its own branch, so the small problems' kernels run
+ * beside the large ones' and the host launches and waits once per batch step. */
 typedef struct pasm_batch pasm_batch;
 
 /* One context per problem p: n_levels[p] levels, A[p], M[p] arrays of
@@ -385,13 +390,23 @@ int pasm_batch_setup(pasm_batch** out, int n_problems, const int* n_levels, cons
                      const pasm_csr* const* M, const pasm_csr* const* P, const pasm_opts* opts, void* stream);
 
 /* Solve every problem p for its k[p] smallest pairs from its coarse start:
- * correction steps of all unfinished problems are launched together until
- * every pair is frozen or opts.max_steps rounds.  Outputs per problem (each
- * array of pointers may be NULL; entries host or device): lambda_out[p] (k[p]),
- * U_out[p] (n_p x k[p]), steps_out[p], status_out[p]; *batch_steps = rounds.
- * Returns PASM_ENOTCONV if any pair is still active (outputs written). */
+ * batch steps (one graph replay each; the graph is captured again only when a
+ * problem finishes) until every pair is frozen or opts.max_steps rounds.
+ * Outputs per problem (each array of pointers may be NULL; entries host or
+ * device): lambda_out[p] (k[p]), U_out[p] (n_p x k[p]), steps_out[p],
+ * status_out[p]; *batch_steps = rounds.  Returns PASM_ENOTCONV if any pair is
+ * still active (outputs written); on every return the caller's stream is
+ * ordered after all work the batch queued. */
 int pasm_batch_solve(pasm_batch* b, const int* k, double tol, double* const* lambda_out, double* const* U_out,
                      int* const* steps_out, int* const* status_out, int* batch_steps);
+
+/* Change the batch's step cap (opts.max_steps at setup); max_steps >= 0, else
+ * PASM_EINVAL. */
+int pasm_batch_set_max_steps(pasm_batch* b, int max_steps);
+
+/* Number of step graphs pasm_batch_solve has captured over the batch's life
+ * (one per change of the set of unfinished problems). */
+int pasm_batch_captures(pasm_batch* b, int* captures);
 
 /* Release the batch and every context in it.  NULL is a no-op. */
 void pasm_batch_destroy(pasm_batch* b);

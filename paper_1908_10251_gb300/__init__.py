@@ -12,7 +12,7 @@ from .capi import (  # noqa: F401
     pasm_trace_step, pasm_trace_launches, pasm_kernel_class_name, pasm_border_noalloc,
     pasm_nn_setup, pasm_nn_get_weights, pasm_nn_apply, pasm_nn_loss_grad, pasm_nn_train,
     pasm_nn_capture_residuals, pasm_nn_accepted, pasm_nn_errors,
-    pasm_batch_setup, pasm_batch_solve, pasm_batch_destroy,
+    pasm_batch_setup, pasm_batch_solve, pasm_batch_captures, pasm_batch_set_max_steps, pasm_batch_destroy,
     PasmError, load_library,
     PASM_PROJ_TENSOR, PASM_PROJ_FP64, PASM_FP64, PASM_MIXED, PASM_ETIMEOUT, PASM_JACOBI, PASM_CG,
 )

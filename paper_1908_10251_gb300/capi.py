@@ -104,6 +104,8 @@ def load_library():
         "pasm_border_noalloc": (I, [I, P, P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, I, P, P, P, P, P, P]),
         "pasm_batch_setup": (I, [ctypes.POINTER(P), I, P, P, P, P, ctypes.POINTER(pasm_opts), P]),
         "pasm_batch_solve": (I, [P, P, ctypes.c_double, P, P, P, P, ctypes.POINTER(I)]),
+        "pasm_batch_captures": (I, [P, ctypes.POINTER(I)]),
+        "pasm_batch_set_max_steps": (I, [P, I]),
         "pasm_batch_destroy": (None, [P]),
         "pasm_destroy": (None, [P]),
         "pasm_strerror": (ctypes.c_char_p, [I]),
@@ -419,6 +421,17 @@ def pasm_batch_solve(batch: Batch, ks, tol: float):
     code = _check(lib.pasm_batch_solve(batch.handle, K, tol, arr(lams), arr(Us), arr(steps), arr(stats),
                                        ctypes.byref(rounds)), "pasm_batch_solve", allow=(PASM_ENOTCONV,))
     return code, lams, Us, steps, stats, rounds.value
+
+
+def pasm_batch_set_max_steps(batch: Batch, max_steps: int):
+    _check(load_library().pasm_batch_set_max_steps(batch.handle, max_steps), "pasm_batch_set_max_steps")
+
+
+def pasm_batch_captures(batch: Batch) -> int:
+    """Step graphs the batch has captured (one per change of the unfinished set)."""
+    n = ctypes.c_int(0)
+    _check(load_library().pasm_batch_captures(batch.handle, ctypes.byref(n)), "pasm_batch_captures")
+    return n.value
 
 
 def pasm_batch_destroy(batch: Batch):

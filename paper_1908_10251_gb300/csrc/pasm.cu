@@ -1098,6 +1098,22 @@ int pasm_step(pasm_ctx* c, int* n_active) {
   return PASM_OK;
 }
 
+// Enqueue one correction step on the context's own stream, with no ordering
+// against the caller's stream, no graph of its own and no synchronisation, so
+// that the batch driver can capture the steps of many contexts into one graph
+// (the step's active count lands in the context's pinned word, read by
+// pasm_ctx_active_host once the work is done).
+int pasm_ctx_enqueue_step(pasm_ctx* c) {
+  if (!c || !c->initialized) return PASM_ESTATE;
+  step_body(c);
+  if (c->opts.precision == PASM_MIXED) c->u_stale = true;
+  return PASM_OK;
+}
+
+void* pasm_ctx_stream(pasm_ctx* c) { return c ? (void*)c->s : nullptr; }
+
+int pasm_ctx_active_host(pasm_ctx* c) { return c && c->h_nact ? *c->h_nact : 0; }
+
 // Wait for the context's queued work and return the active-pair count the
 // last step left in pinned memory (used by the batch driver).
 int pasm_ctx_wait_active(pasm_ctx* c, int* n_active) {
@@ -1135,8 +1151,11 @@ int pasm_ctx_guard_freezes(pasm_ctx* c, int* n_active) {
   std::vector<int> status((size_t)k, 0), active((size_t)k, 0);
   int r = pasm_residuals(c, res.data());
   if (r) return r;
-  CK(cudaMemcpy(status.data(), c->status, sizeof(int) * k, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(active.data(), c->active, sizeof(int) * k, cudaMemcpyDeviceToHost));
+  // copies on the context's stream (non-blocking: the legacy-stream cudaMemcpy would not be
+  // ordered with it), completed before the host reads or the next step runs
+  CK(cudaMemcpyAsync(status.data(), c->status, sizeof(int) * k, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaMemcpyAsync(active.data(), c->active, sizeof(int) * k, cudaMemcpyDeviceToHost, c->s));
+  CK(cudaStreamSynchronize(c->s));
   int back = 0;
   for (int i = 0; i < k; ++i)
     if (status[(size_t)i] == PASM_PAIR_CONVERGED && !(res[(size_t)i] <= c->opts.res_tol)) {
@@ -1145,8 +1164,9 @@ int pasm_ctx_guard_freezes(pasm_ctx* c, int* n_active) {
       ++back;
     }
   if (back) {
-    CK(cudaMemcpy(c->status, status.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->active, active.data(), sizeof(int) * k, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(c->status, status.data(), sizeof(int) * k, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->active, active.data(), sizeof(int) * k, cudaMemcpyHostToDevice, c->s));
+    CK(cudaStreamSynchronize(c->s));
     if (n_active) *n_active += back;
   }
   return PASM_OK;

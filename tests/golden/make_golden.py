@@ -49,11 +49,14 @@ def write(name):
 
 HISTORIES = {
     # name: (dim, N_fine, N_coarse, k, tol, max_steps, nested start)
+    "square_h64_H8_k8_history": (2, 64, 8, 8, 1e-10, 60, False),
+    "square_h64_H8_k8_nofreeze_history": (2, 64, 8, 8, 0.0, 40, False),
     "square_h1024_H16_k64_history": (2, 1024, 16, 64, 1e-10, 40, False),
     "square_h1024_H16_k64_nested_history": (2, 1024, 16, 64, 1e-10, 40, True),
     "cube_h128_H8_k32_history": (3, 128, 8, 32, 1e-10, 30, False),
     # no freezing (tol 0): shows which converged pairs are stable fixed points of the correction
     "cube_h128_H8_k32_nofreeze_history": (3, 128, 8, 32, 0.0, 40, False),
+    "square_h1024_H16_k64_nofreeze_history": (2, 1024, 16, 64, 0.0, 40, False),
 }
 
 

@@ -98,3 +98,22 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
         steps = 1
     bench.main_reference(Args())
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_pool_matches_sequential_oracle():
+    """The pair-parallel CPU baseline (worker processes, pairs split evenly)
+    computes exactly the oracle's own iterates: pairs are independent
+    (Section 3.2), so splitting them over processes changes nothing."""
+    import meshgen as mg
+    import oracle
+    work = {"dim": 2, "N": 32, "NH": 8, "k": 6, "tol": 1e-10}
+    pool = bench.OraclePool(work, procs=2)
+    try:
+        assert pool.procs == 2 and sorted(sum(pool.cols, [])) == list(range(6))
+        dts = [pool.step() for _ in range(3)]
+    finally:
+        pool.close()
+    assert all(dt > 0 for dt in dts)
+    prob = oracle.Problem.from_hierarchy(mg.build_hierarchy(2, 32, 8))
+    _, _, _, hist = oracle.solve(prob, 6, tol=1e-10, max_steps=3, history=True)
+    assert np.allclose(np.array(pool.history), np.array(hist), rtol=1e-14, atol=0)

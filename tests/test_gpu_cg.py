@@ -12,8 +12,10 @@ must reach the oracle's converged eigenvalues to 1e-9.
 import numpy as np
 import pytest
 
+import gpu_accuracy as ga
 import meshgen as mg
 import oracle
+from paper_1908_10251_gb300 import accuracy as acc
 from oracle import pasm as op
 
 torch = pytest.importorskip("torch")
@@ -76,25 +78,31 @@ def test_cg_correction_steps_parity_fp64(pg):
         assert colrel(Ug, U) < 1e-8, step
 
 
-def test_cg_mixed_precision_reaches_oracle(pg):
-    """Mixed precision with CG smoothing converges to the oracle's converged
-    eigenvalues (1e-9) and eigenvectors (energy-norm error 1e-5)."""
+def test_cg_mixed_precision_final_state(pg):
+    """Mixed precision with CG smoothing, 40 steps with no pair frozen: at the
+    end every pair the float64 oracle converges (without freezing, 40 steps)
+    is within 1e-9 of the oracle's eigenvalue and of the ARPACK reference of
+    its cluster, distinct, and within an M-principal angle of 1e-6 of both the
+    reference eigenspace and the oracle's vectors."""
     H = mg.build_hierarchy(2, 64, 8)
-    ctx = setup_ctx(pg, H, precision=1)
+    ctx = setup_ctx(pg, H, precision=1, max_steps=40)
     prob = oracle.Problem.from_hierarchy(H, smoother="cg")
     k = 5
-    lam_o, U_o, _, _ = oracle.solve(prob, k, tol=1e-12, max_steps=80)
+    lam_o, U_o, _, _ = oracle.solve(prob, k, tol=0.0, max_steps=40)
+    A, M = H.fine.A, H.fine.M
+    ref, vecs = acc.reference_pairs(A, M, k + 6, acc.stencil_inverse(A, 2, 64))
+    pset = np.where(acc.cluster_errors(lam_o, ref) <= 1e-9)[0]
+    assert len(pset) >= 4
     lam = np.zeros(k)
     U = np.zeros((H.fine.n, k))
     steps = np.zeros(k, dtype=np.int32)
     status = np.zeros(k, dtype=np.int32)
-    pg.pasm_solve(ctx, k, 1e-12, None, None, lam, U, steps, status)
-    assert np.allclose(lam, lam_o, rtol=1e-9)
-    A = H.fine.A
-    for i in range(k):
-        u = U[:, i] * np.sign(U[:, i] @ U_o[:, i])
-        e = u - U_o[:, i]
-        assert np.sqrt(e @ (A @ e)) < 1e-5
+    pg.pasm_solve(ctx, k, 0.0, None, None, lam, U, steps, status)
+    assert np.all(steps == 40)
+    assert np.allclose(lam[pset], lam_o[pset], rtol=1e-9)
+    ga.check_final(M, lam, U, ref, vecs, pset)
+    for i in pset:
+        assert acc.angle_to(M, U[:, [i]], U_o[:, [i]]) <= 1e-6, i
 
 
 def test_cg_zero_and_ragged_columns(pg):

@@ -6,8 +6,10 @@ CSR values and stencil differ from Example 1.  Tolerances as for Example 1."""
 import numpy as np
 import pytest
 
+import gpu_accuracy as ga
 import meshgen as mg
 import oracle
+from paper_1908_10251_gb300 import accuracy as acc
 from oracle import pasm as op
 
 torch = pytest.importorskip("torch")
@@ -60,18 +62,24 @@ def test_example2_steps_parity_fp64(pg, ex2):
 
 
 @pytest.mark.parametrize("smoother", [0, 2])
-def test_example2_mixed_reaches_oracle(pg, ex2, smoother):
-    """Mixed precision (Jacobi or CG smoothing) converges to the oracle's
-    converged eigenvalues to 1e-9."""
-    ctx = setup_ctx(pg, ex2, precision=1, smoother=smoother)
+def test_example2_mixed_final_state(pg, ex2, smoother):
+    """Mixed precision (Jacobi or CG smoothing), 40 steps with no pair frozen:
+    at the end every pair the float64 oracle converges (40 steps, no freezing)
+    is within 1e-9 of the oracle's eigenvalue and of the ARPACK reference of
+    its cluster, distinct, and within an M-principal angle of 1e-6 of the
+    reference eigenspace (shift-invert with a sparse LU of A)."""
+    ctx = setup_ctx(pg, ex2, precision=1, smoother=smoother, max_steps=40)
     prob = oracle.Problem.from_hierarchy(ex2, smoother="cg" if smoother == 2 else "jacobi")
     k = 6
-    lam_o, _, steps_o, _ = oracle.solve(prob, k, tol=1e-12, max_steps=60)
-    conv = steps_o < 60
-    assert conv.sum() >= 4
+    lam_o, _, _, _ = oracle.solve(prob, k, tol=0.0, max_steps=40)
+    A, M = ex2.fine.A, ex2.fine.M
+    ref, vecs = acc.reference_pairs(A, M, k + 6, ga.lu_inverse(A))
+    pset = np.where(acc.cluster_errors(lam_o, ref) <= 1e-9)[0]
+    assert len(pset) >= 4
     lam = np.zeros(k)
     U = np.zeros((ex2.fine.n, k))
     steps = np.zeros(k, dtype=np.int32)
     status = np.zeros(k, dtype=np.int32)
-    pg.pasm_solve(ctx, k, 1e-12, None, None, lam, U, steps, status)
-    assert np.allclose(lam[conv], lam_o[conv], rtol=1e-9)
+    pg.pasm_solve(ctx, k, 0.0, None, None, lam, U, steps, status)
+    assert np.allclose(lam[pset], lam_o[pset], rtol=1e-9)
+    ga.check_final(M, lam, U, ref, vecs, pset)

@@ -66,3 +66,57 @@ def test_border_noalloc_rejects_bad_sizes():
         with pytest.raises(pg.PasmError) as ei:
             pg.pasm_border_noalloc(2, zi, zi, z, zi, zi, z, kk, z, z, z, z, z)
         assert ei.value.code == 1
+
+
+def test_border_noalloc_widest_block_capped_grid():
+    """The widest block the entry point accepts (k = 256) on the h = 1/1024
+    square (1,046,529 rows): the grid is capped by the fixed scratch (304
+    blocks of 8 rows for 130,817 row groups), so every block walks many rows.
+    Against scipy's A X, M X and float64 column dot products on the host, and
+    against the bordering of the context path (pasm_augmented, H = 1/32 so
+    that k <= N_H), on two calls in a row; a warm call changes the device's
+    free memory by nothing."""
+    from paper_1908_10251_gb300 import build
+    build.build()
+    import paper_1908_10251_gb300 as pg
+    pg.load_library()
+    H = mg.build_hierarchy(2, 1024, 32)
+    A, M = H.fine.A, H.fine.M
+    n, k = A.shape[0], 256
+    stream = torch.cuda.current_stream()
+    dev = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")  # noqa: E731
+    Arp, Aci, Aval = dev(A.indptr, torch.int32), dev(A.indices, torch.int32), dev(A.data, torch.float64)
+    Mrp, Mci, Mval = dev(M.indptr, torch.int32), dev(M.indices, torch.int32), dev(M.data, torch.float64)
+    YA = torch.empty((n, k), dtype=torch.float64, device="cuda")
+    YM = torch.empty_like(YA)
+    beta = torch.empty(k, dtype=torch.float64, device="cuda")
+    zeta = torch.empty(k, dtype=torch.float64, device="cuda")
+    ctx = pg.pasm_setup([lv.A for lv in H.levels], [lv.M for lv in H.levels], H.P, pg.pasm_default_opts(),
+                        stream.cuda_stream)
+    lam = np.linspace(20.0, 2000.0, k)
+    pg.pasm_init(ctx, k, 0.0)
+    for seed in (11, 12):
+        Xh = np.random.default_rng(seed).standard_normal((n, k))
+        X = dev(Xh, torch.float64)
+        args = (n, Arp, Aci, Aval, Mrp, Mci, Mval, k, X, YA, YM, beta, zeta, stream.cuda_stream)
+        pg.pasm_border_noalloc(*args)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        pg.pasm_border_noalloc(*args)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        ya_ref, ym_ref = A @ Xh, M @ Xh
+        ya, ym = YA.cpu().numpy(), YM.cpu().numpy()
+        assert np.abs(ya - ya_ref).max() <= 1e-13 * np.abs(ya_ref).max()
+        assert np.abs(ym - ym_ref).max() <= 1e-13 * np.abs(ym_ref).max()
+        del ya, ym
+        b_ref = np.einsum("ij,ij->j", Xh, ya_ref)
+        z_ref = np.einsum("ij,ij->j", Xh, ym_ref)
+        assert np.allclose(beta.cpu().numpy(), b_ref, rtol=1e-12, atol=0)
+        assert np.allclose(zeta.cpu().numpy(), z_ref, rtol=1e-12, atol=0)
+        beta_ctx = np.zeros(k); zeta_ctx = np.zeros(k)
+        pg.pasm_augmented(ctx, lam, Xh, None, None, beta_ctx, zeta_ctx)
+        assert np.allclose(beta.cpu().numpy(), beta_ctx, rtol=1e-12, atol=0)
+        assert np.allclose(zeta.cpu().numpy(), zeta_ctx, rtol=1e-12, atol=0)
+        del Xh, X, ya_ref, ym_ref
+    pg.pasm_destroy(ctx)
