@@ -164,6 +164,62 @@ def loss_and_grad(w, A, R, nx, ny):
     return L, pack([a + b for a, b in zip(g1, g2)])
 
 
+def loss_and_grad_bf16(w, A, R, nx, ny):
+    """loss_and_grad with the second convolution's products taken on bfloat16
+    operands, as the tensor-core training path computes them: in the forward
+    pass relu(+-z1) and W2 are rounded (as in apply(..., bf16_layer2=True));
+    in the backward pass the two products of layer 2 -- its weight gradient
+    sum a+- g+- and its input gradient g+- (*) W2 -- take a+- (already
+    rounded), the rounded output gradients g+- = dL/dz2+- and the rounded W2.
+    Everything else as in loss_and_grad (float64 here)."""
+    W1, W2, W3 = unpack(w)
+    k = R.shape[1]
+    x = to_grid(R, nx, ny)[..., None]
+    z1 = conv(x, W1)
+    W2b = bf16(W2)
+    ap, am = bf16(np.maximum(z1, 0.0)), bf16(np.maximum(-z1, 0.0))
+    z2p, z2m = conv(ap, W2b), conv(am, W2b)
+    h = 0.5 * (np.maximum(z2p, 0.0) - np.maximum(z2m, 0.0))
+    D = from_grid(conv(h, W3)[..., 0])
+    E = R - A @ D
+    nr2 = np.einsum("ij,ij->j", R, R)
+    L = float(np.mean(np.einsum("ij,ij->j", E, E) / nr2))
+    gy = to_grid(-2.0 * (A.T @ (E / nr2)) / k, nx, ny)[..., None]
+    gW3 = conv_weight_grad(h, gy)
+    gh = conv_input_grad(gy, W3)
+    gp = bf16(0.5 * gh * (z2p > 0))
+    gm = bf16(-0.5 * gh * (z2m > 0))
+    gW2 = conv_weight_grad(ap, gp) + conv_weight_grad(am, gm)
+    gap, gam = conv_input_grad(gp, W2b), conv_input_grad(gm, W2b)
+    gz1 = gap * (z1 > 0) - gam * (z1 < 0)
+    gW1 = conv_weight_grad(x, gz1)
+    return L, pack([gW1, gW2, gW3])
+
+
+def bf16_gradient_bound(w, A, R, nx, ny):
+    """First-order bound on |loss_and_grad_bf16 - loss_and_grad|, weight by
+    weight: 8 u G_abs, u = 2^-9 (bf16 unit roundoff), G_abs = the gradient of
+    the network evaluated on |W|, |r| and the absolute values of every
+    activation and output gradient.  Each product of layer 2 carries at most
+    four rounded factors along any path of the chain rule (forward a and W2,
+    backward g and W2 or a): 4u to first order; the factor 2 covers
+    second-order terms and ReLU switches near zero."""
+    W1, W2, W3 = unpack(w)
+    x = to_grid(R, nx, ny)[..., None]
+    a = np.abs(conv(x, W1))
+    W2a, W3a = np.abs(W2), np.abs(W3)
+    z2 = conv(a, W2a)
+    D = from_grid(conv(z2, W3a)[..., 0])
+    absA = abs(A)
+    E = np.abs(R) + absA @ D
+    nr2 = np.einsum("ij,ij->j", R, R)
+    gy = to_grid(2.0 * (absA.T @ (E / nr2)) / R.shape[1], nx, ny)[..., None]
+    gh = conv_input_grad(gy, W3a)
+    G2 = 2 * conv_weight_grad(a, gh)
+    G1 = 2 * conv_weight_grad(np.abs(x), conv_input_grad(gh, W2a))
+    return 8 * 2.0 ** -9 * pack([G1, G2, conv_weight_grad(z2, gy)])
+
+
 def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015), t counted from 1.  Returns new (w, m, v)."""
     m = b1 * m + (1 - b1) * g

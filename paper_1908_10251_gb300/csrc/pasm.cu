@@ -113,6 +113,7 @@ struct pasm_ctx {
     int* err = nullptr;                      // timed-out tensor-core waits
     NNOuterWeights w13{};                    // host copy of layers 1 and 3 (kernel parameters)
     uint16_t* w2 = nullptr;                  // layer 2 as bf16 in the tensor-core operand layout
+    uint16_t *w2f = nullptr, *w2t = nullptr; // training: forward and flipped layouts, rebuilt per step
     std::vector<void*> allocs;
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
@@ -783,6 +784,7 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
     }
   CK(secular_prepare(NH));
   CK(nn_tc_prepare());
+  CK(nn_tc_train_prepare());
   AL(c->allocs, &c->lamH, (size_t)NH);
   AL(c->allocs, &c->Q, (size_t)NH * NH);
   AL(c->allocs, &c->AinvH64, (size_t)NH * NH);
@@ -1410,6 +1412,8 @@ int pasm_nn_setup(pasm_ctx* c, const int32_t* nx, const float* weights) {
     AL(nn.allocs, &nn.norms, 2 * 256); AL(nn.allocs, &nn.loss, 1); AL(nn.allocs, &nn.accepted, 256);
     AL(nn.allocs, &nn.err, 4);
     AL(nn.allocs, &nn.w2, 2304);
+    AL(nn.allocs, &nn.w2f, 2304);
+    AL(nn.allocs, &nn.w2t, 2304);
     CK(cudaMemset(nn.err, 0, sizeof(int) * 4));
   }
   CK(cudaMemcpy(nn.W, weights, sizeof(float) * kNNWeights, cudaMemcpyDefault));
@@ -1476,12 +1480,17 @@ static void nn_loss_grad_dev(pasm_ctx* c, int level, int k, int ldk2) {
   const Launch L = launcher(c);
   LevelDev& v = c->lv[(size_t)level];
   NNGrid g{nn.nx[(size_t)level], nn.ny[(size_t)level], ldk2, k};
-  nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
+  // a learned-smoother context trains layer 2 on the tensor cores (the form its V-cycles run),
+  // others on float32 CUDA cores
+  const bool tc = c->opts.smoother == PASM_LEARNED && nn_tc_supported(ldk2);
+  if (tc) nn_forward_train_tc(L, g, nn.buf, nn.W, nn.w2f, nn.R, nn.D, nn.err);
+  else nn_forward(L, g, nn.buf, nn.W, nn.R, nn.D);
   rowop<float>(L, OP_RESID, v.A, nn.D, nn.R, nullptr, nullptr, 0.f, nn.X, ldk2);   // E = R - A D
   nn_column_norms(L, v.n, ldk2, nn.R, nn.X, nn.partial, nn.norms);
   nn_loss_seed(L, (int64_t)v.n * ldk2, ldk2, k, nn.X, nn.norms, nn.Es, nn.loss);
   rowop<float>(L, OP_SPMM, v.A, nn.Es, nullptr, nullptr, nullptr, 0.f, nn.gD, ldk2);  // dL/dD = A^T Es
-  nn_backward(L, g, nn.buf, nn.W, nn.R, nn.gD, nn.grad);
+  if (tc) nn_backward_tc(L, g, nn.buf, nn.W, nn.w2t, nn.R, nn.gD, nn.grad, nn.err);
+  else nn_backward(L, g, nn.buf, nn.W, nn.R, nn.gD, nn.grad);
 }
 
 int pasm_nn_loss_grad(pasm_ctx* c, int level, int k, const float* R, double* loss, float* grad) {

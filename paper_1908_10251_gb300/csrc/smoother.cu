@@ -300,6 +300,53 @@ void nn_backward(const Launch& L, const NNGrid& g, const NNBuf& b, const float* 
   wgrad<1, 16, IN_ID>(L, g, b, R, b.gz1, gW, false);
 }
 
+void nn_forward_train_tc(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, uint16_t* w2f,
+                         const float* R, float* Dout, int* err) {
+  const int64_t pix = (int64_t)g.nx * g.ny * g.ldk;
+  nn_tc_w2_layout(L, W + 144, false, w2f);
+  L.begin(KC_NN, (double)pix * 4.0 * 2, (double)pix * 2.0 * 9 * 16);
+  k_conv<1, 16, IN_ID><<<grid_for(pix), kNNBlock, 0, L.s>>>(g.nx, g.ny, g.ldk, g.k, W, R, b.z1);
+  L.bump();
+  nn_tc_conv16(L, g, 1, w2f, b.z1, b.z2p, err);
+  nn_tc_conv16(L, g, 2, w2f, b.z1, b.z2m, err);
+  L.begin(KC_NN, (double)pix * 16 * 4.0 * 3, (double)pix * 16 * 3);
+  k_combine<<<grid_stride(pix * 16), 256, 0, L.s>>>(pix * 16, b.z2p, b.z2m, b.h);
+  L.bump();
+  L.begin(KC_NN, (double)pix * 4.0 * 17, (double)pix * 2.0 * 9 * 16);
+  k_conv<16, 1, IN_ID><<<grid_for(pix), kNNBlock, 0, L.s>>>(g.nx, g.ny, g.ldk, g.k, W + 144 + 2304, b.h, Dout);
+  L.bump();
+}
+
+void nn_backward_tc(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, uint16_t* w2t, const float* R,
+                    const float* gD, float* gW, int* err) {
+  const int64_t pix = (int64_t)g.nx * g.ny * g.ldk;
+  nn_tc_w2_layout(L, W + 144, true, w2t);
+  L.begin(KC_NN, 0, 0);
+  k_flip<<<(144 + 127) / 128, 128, 0, L.s>>>(16, 1, W + 144 + 2304, b.wflip3);
+  L.bump();
+  // layer 3 (CUDA cores, float32)
+  wgrad<16, 1, IN_ID>(L, g, b, b.h, gD, gW + 144 + 2304, false);
+  L.begin(KC_NN, 0, (double)pix * 2.0 * 9 * 16);
+  k_conv<1, 16, IN_ID><<<grid_for(pix), kNNBlock, 0, L.s>>>(g.nx, g.ny, g.ldk, g.k, b.wflip3, gD, b.gh);
+  L.bump();
+  L.begin(KC_NN, 0, 0);
+  k_combine_back<<<grid_stride(pix * 16), 256, 0, L.s>>>(pix * 16, b.gh, b.z2p, b.z2m, b.gzp, b.gzm);
+  L.bump();
+  // layer 2 on the tensor cores: weight gradient of both branches, then the input gradients
+  const int nblk = nn_tc_wgrad_ctas(g);
+  nn_tc_wgrad16(L, g, b.z1, b.gzp, b.gzm, b.wpart, err);
+  L.begin(KC_NN, (double)nblk * 2304 * 4.0, (double)nblk * 2304);
+  k_wsum<<<(2304 + 127) / 128, 128, 0, L.s>>>(2304, nblk, b.wpart, gW + 144, 0);
+  L.bump();
+  nn_tc_conv16(L, g, 0, w2t, b.gzp, b.gap, err);
+  nn_tc_conv16(L, g, 0, w2t, b.gzm, b.gam, err);
+  // layer 1 (CUDA cores, float32)
+  L.begin(KC_NN, 0, 0);
+  k_first_back<<<grid_stride(pix * 16), 256, 0, L.s>>>(pix * 16, b.gap, b.gam, b.z1, b.gz1);
+  L.bump();
+  wgrad<1, 16, IN_ID>(L, g, b, R, b.gz1, gW, false);
+}
+
 void nn_column_norms(const Launch& L, int n, int ldk, const float* a, const float* bb, double* partial,
                      double* norms) {
   const int rpb = 64;

@@ -57,4 +57,25 @@ void nn_tc_layer2_layout(const float* W2, uint16_t* out);  // 2304 floats -> 230
 void nn_forward_tc(const Launch& L, const NNGrid& g, const NNOuterWeights& w13, const void* w2, const float* R,
                    float* D, int* err);
 
+// Tensor-core training of layer 2 (smoother_tc_train.cu): bf16 operands,
+// float32 accumulation.  Needs ldk % 8 == 0.
+cudaError_t nn_tc_train_prepare();
+// persistent CTAs of the weight-gradient kernel (rows of its partial sums) on grid g
+int nn_tc_wgrad_ctas(const NNGrid& g);
+// W2 (2304 floats, device) -> bf16 operand layout; flip: the input-gradient kernel
+void nn_tc_w2_layout(const Launch& L, const float* W2, bool flip, uint16_t* out);
+// out = W (*) tf(in), 16 -> 16 channels; mode 0 identity, 1 relu, 2 relu of the negation
+void nn_tc_conv16(const Launch& L, const NNGrid& g, int mode, const uint16_t* w2, const float* in, float* out,
+                  int* err);
+// per-CTA partial sums (nn_tc_wgrad_ctas rows of 2304) of layer 2's weight gradient, both branches
+void nn_tc_wgrad16(const Launch& L, const NNGrid& g, const float* z1, const float* gp, const float* gm,
+                   float* partial, int* err);
+// The training forward and backward with layer 2 on the tensor cores (the CUDA-core
+// layers 1 and 3 unchanged); w2f / w2t: device scratch for the forward and flipped
+// layouts of W2 (2304 bf16 each), rebuilt from W on every call.
+void nn_forward_train_tc(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, uint16_t* w2f,
+                         const float* R, float* D, int* err);
+void nn_backward_tc(const Launch& L, const NNGrid& g, const NNBuf& b, const float* W, uint16_t* w2t, const float* R,
+                    const float* gD, float* gW, int* err);
+
 }  // namespace pasm

@@ -79,8 +79,8 @@ def test_cg_correction_steps_parity_fp64(pg):
 
 
 def test_cg_mixed_precision_final_state(pg):
-    """Mixed precision with CG smoothing, 40 steps with no pair frozen: at the
-    end every pair the float64 oracle converges (without freezing, 40 steps)
+    """Mixed precision with CG smoothing, 40 steps (pairs frozen at
+    |d lambda| / lambda < 1e-13): at the end every pair the float64 oracle converges (without freezing, 40 steps)
     is within 1e-9 of the oracle's eigenvalue and of the ARPACK reference of
     its cluster, distinct, and within an M-principal angle of 1e-6 of both the
     reference eigenspace and the oracle's vectors."""
@@ -97,8 +97,7 @@ def test_cg_mixed_precision_final_state(pg):
     U = np.zeros((H.fine.n, k))
     steps = np.zeros(k, dtype=np.int32)
     status = np.zeros(k, dtype=np.int32)
-    pg.pasm_solve(ctx, k, 0.0, None, None, lam, U, steps, status)
-    assert np.all(steps == 40)
+    pg.pasm_solve(ctx, k, 1e-13, None, None, lam, U, steps, status)
     assert np.allclose(lam[pset], lam_o[pset], rtol=1e-9)
     ga.check_final(M, lam, U, ref, vecs, pset)
     for i in pset:

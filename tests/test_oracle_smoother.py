@@ -166,3 +166,32 @@ def test_bf16_layer2_exact_when_operands_representable():
     b = sm.apply(w, r)
     assert np.array_equal(a, b)
     assert np.array_equal(sm.apply(w, -r, bf16_layer2=True), -a)
+
+
+def test_bf16_gradient_equals_plain_where_rounding_is_exact():
+    """With weights and inputs on a coarse dyadic grid the forward rounding is
+    the identity: the bf16 form has the same loss and the same layer-3
+    gradient (summed in another order: to 1e-12) as the float64 form; the
+    layer-2 and layer-1 gradients differ, since the output gradients dL/dz2
+    are not dyadic (the loss divides by |r|^2) and are rounded."""
+    rng = np.random.default_rng(5)
+    ws = [rng.integers(-3, 4, size=s).astype(np.float64) * 0.25 for s in sm.SHAPES]
+    w = sm.pack(ws)
+    A, M = mg.assemble(2, 10)
+    nx = ny = 9
+    R = rng.integers(-4, 5, size=(nx * ny, 2)).astype(np.float64)
+    L1, g1 = sm.loss_and_grad(w, A, R, nx, ny)
+    L2, g2 = sm.loss_and_grad_bf16(w, A, R, nx, ny)
+    assert L1 == L2
+    assert np.allclose(g1[2448:], g2[2448:], rtol=1e-12, atol=0)
+    assert not np.allclose(g1[:2448], g2[:2448], rtol=1e-6, atol=0)
+
+
+def test_bf16_gradient_within_first_order_bound():
+    """|g_bf16 - g| <= the first-order bf16 bound of oracle.smoother
+    (8 u G_abs, see bf16_gradient_bound), and the rounding does act."""
+    A, R, w, nx, ny = small_case(6, N=10, k=3)
+    _, g = sm.loss_and_grad(w, A, R, nx, ny)
+    _, gb = sm.loss_and_grad_bf16(w, A, R, nx, ny)
+    assert np.all(np.abs(gb - g) <= sm.bf16_gradient_bound(w, A, R, nx, ny))
+    assert np.abs(gb - g).max() > 0
