@@ -18,6 +18,44 @@ def smallest_eigenvalues(A, M, count: int, extra: int = 8, tol: float = 1e-14):
     return np.sort(vals)[:count]
 
 
+def laplacian_inverse(dim: int, N: int):
+    """A^{-1} for the constant-coefficient P1 stiffness of the uniform meshes
+    (the 5-point stencil (4, -1) of the right-triangle mesh of the square,
+    h times the 7-point stencil (6, -1) of the Kuhn mesh of the cube): the
+    grid sine functions sin(m pi x) ... are its eigenvectors with eigenvalues
+    sum_d (2 - 2 cos(m_d pi h)) (times h in 3D), so the inverse is a type-I
+    discrete sine transform, a division, and the inverse transform.  Interior
+    nodes x fastest, as meshgen numbers them."""
+    import scipy.fft as sfft
+    lam1 = 2.0 - 2.0 * np.cos(np.pi * np.arange(1, N) / N)
+    grids = np.meshgrid(*([lam1] * dim), indexing="ij")
+    sym = sum(grids) * (1.0 / N if dim == 3 else 1.0)          # index order (z, y, x) or (y, x)
+    shape = (N - 1,) * dim
+
+    def apply(b):
+        b = np.asarray(b, dtype=np.float64)
+        cols = b.reshape(b.shape[0], -1).T.reshape((-1,) + shape)
+        axes = tuple(range(1, dim + 1))
+        x = sfft.idstn(sfft.dstn(cols, type=1, axes=axes) / sym[None], type=1, axes=axes)
+        return x.reshape(x.shape[0], -1).T.reshape(b.shape)
+    return apply
+
+
+def smallest_eigenvalues_sine(dim: int, N: int, count: int, extra: int = 8, tol: float = 1e-14, seed: int = 0):
+    """The `count` smallest eigenvalues of the constant-coefficient pencil by
+    ARPACK in shift-invert mode around 0, with the exact sine-transform A^{-1}
+    (meshes too large to factorise)."""
+    import meshgen as mg
+    A, M = mg.assemble(dim, N)
+    n = A.shape[0]
+    inv = laplacian_inverse(dim, N)
+    op = spla.LinearOperator((n, n), matvec=inv, matmat=inv, dtype=np.float64)
+    v0 = np.random.default_rng(seed).standard_normal(n)
+    vals = spla.eigsh(A, k=count + extra, M=M, sigma=0.0, which="LM", OPinv=op, tol=tol, v0=v0,
+                      return_eigenvectors=False)
+    return np.sort(vals)[:count]
+
+
 def smallest_eigenvalues_lobpcg(hier, count: int, extra: int = 8, tol: float = 1e-10, maxiter: int = 400,
                                 seed: int = 0):
     """The `count` smallest eigenvalues of the finest pencil of a hierarchy by

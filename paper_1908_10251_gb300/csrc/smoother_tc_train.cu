@@ -137,25 +137,33 @@ __global__ void __launch_bounds__(kThreads) k_tc_conv16(int nx, int ny, int ldk,
   if (warp == 0) tmem_alloc(tmem_slot, kConvTmem);
   for (int t = tid; t < kConvW / 16; t += kThreads)
     *reinterpret_cast<uint4*>(W + 16 * t) = __ldg(reinterpret_cast<const uint4*>(w2g) + t);
-  // input tile: thread item = (pixel, pair, channel half): 8 floats -> 8 bf16 (one 16-byte row)
-  for (int t = tid; t < IR * IW * PB * 2; t += kThreads) {
-    const int half = t & 1, q = (t >> 1) % PB, pix = (t >> 1) / PB;
+  // input tile: thread item = (pixel, pair): its 16 channels (64 contiguous bytes, so a warp reads
+  // 2 KB in one sweep) -> two 16-byte rows of 8 bf16, one per channel half; consecutive threads
+  // store consecutive rows of one plane (no bank conflicts)
+#pragma unroll 2
+  for (int t = tid; t < IR * IW * PB; t += kThreads) {
+    const int q = t % PB, pix = t / PB;
     const int col = pix % IW, row = pix / IW;
     const int x = x0 - 1 + col, y = y0 - 1 + row, c = c0 + q;
-    float v[8];
+    float4 u[4];
     if (x >= 0 && x < nx && y >= 0 && y < ny && c < k) {
-      const float4* src = reinterpret_cast<const float4*>(in + (((int64_t)y * nx + x) * ldk + c) * 16 + half * 8);
-      const float4 u0 = __ldg(src), u1 = __ldg(src + 1);
-      v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w; v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+      const float4* src = reinterpret_cast<const float4*>(in + (((int64_t)y * nx + x) * ldk + c) * 16);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) u[i] = __ldg(src + i);
     } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      for (int i = 0; i < 4; ++i) u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __align__(16) __nv_bfloat162 b[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = __floats2bfloat162_rn(tf<MODE>(v[2 * i]), tf<MODE>(v[2 * i + 1]));
-    *reinterpret_cast<uint4*>(A + half * kConvPlane + ((row * IW + col) * PB + q) * 16) =
-        *reinterpret_cast<uint4*>(b);
+    for (int half = 0; half < 2; ++half) {
+      const float4 a = u[2 * half], b = u[2 * half + 1];
+      __align__(16) __nv_bfloat162 v[4];
+      v[0] = __floats2bfloat162_rn(tf<MODE>(a.x), tf<MODE>(a.y));
+      v[1] = __floats2bfloat162_rn(tf<MODE>(a.z), tf<MODE>(a.w));
+      v[2] = __floats2bfloat162_rn(tf<MODE>(b.x), tf<MODE>(b.y));
+      v[3] = __floats2bfloat162_rn(tf<MODE>(b.z), tf<MODE>(b.w));
+      *reinterpret_cast<uint4*>(A + half * kConvPlane + t * 16) = *reinterpret_cast<uint4*>(v);
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");

@@ -565,3 +565,18 @@ def test_gaussian_field_statistics():
     for t, offs in enumerate(tri):
         mean = sum(g[o[0]:o[0] + 16, o[1]:o[1] + 16] for o in offs) / 3.0
         assert np.allclose(kap[t], np.exp(mean), rtol=1e-14)
+
+
+@pytest.mark.parametrize("dim,N", [(2, 12), (3, 6)])
+def test_sine_transform_inverse_and_reference(dim, N):
+    """The oracle's sine-transform inverse of the constant-coefficient stiffness
+    equals a sparse LU solve, and the eigenvalues it gives ARPACK equal the
+    dense generalized eigensolver's."""
+    from oracle.reference import laplacian_inverse, smallest_eigenvalues_sine
+    A, M = mg.assemble(dim, N)
+    B = np.random.default_rng(2).standard_normal((A.shape[0], 2))
+    X = laplacian_inverse(dim, N)(B)
+    assert np.abs(X - spla.splu(A.tocsc()).solve(B)).max() <= 1e-12 * np.abs(X).max()
+    vals = smallest_eigenvalues_sine(dim, N, 6)
+    dense = sla.eigh(A.toarray(), M.toarray(), eigvals_only=True)[:6]
+    assert np.allclose(vals, dense, rtol=1e-12)
