@@ -341,6 +341,15 @@ int pasm_nn_accepted(pasm_ctx* ctx, int* counts);
  * timed out (their output was left unwritten) since pasm_nn_setup. */
 int pasm_nn_errors(pasm_ctx* ctx, int* count);
 
+/* Test hook of the tensor-core projection's bounded completion wait (its MMAs
+ * commit to an mbarrier that one thread polls at most `wait_limit` times; 0 =
+ * the library's limit, about 4 million polls).  With skip_mma != 0 the kernel
+ * issues no MMA, so nothing arrives on that mbarrier and the wait runs out with
+ * nothing in flight: pasm_project then returns PASM_ETIMEOUT and leaves its
+ * outputs unspecified, and the context stays usable.  (0, 0) restores normal
+ * operation.  Drops the context's captured step graph.  Errors: PASM_EINVAL. */
+int pasm_debug_waits(pasm_ctx* ctx, int skip_mma, int wait_limit);
+
 /* Bordering products of the correction step for callers that cannot allocate
  * device memory.  The paper has no counterpart to this entry point: it exists
  * for hosts that reserve the whole device heap for their own pool, that must

@@ -87,6 +87,7 @@ def load_library():
         "pasm_secular_stats": (I, [P, P]),
         "pasm_residuals": (I, [P, P]),
         "pasm_tiles": (I, [P, I, P]),
+        "pasm_debug_waits": (I, [P, I, I]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "pasm_last_launches": (I, [P, ctypes.POINTER(I)]),
@@ -225,6 +226,11 @@ def pasm_augmented(ctx: Context, lam_prev, Uhat, lambda_out=None, U_out=None, be
 def pasm_project(ctx: Context, b, c, bq, cq):
     """bq = Q^T b, cq = Q^T c (N_H x k each, host or device)."""
     _check(load_library().pasm_project(ctx.handle, _ptr(b), _ptr(c), _ptr(bq), _ptr(cq)), "pasm_project")
+
+
+def pasm_debug_waits(ctx: Context, skip_mma: int, wait_limit: int):
+    """Test hook: make the projection's bounded completion wait run out (see include/pasm.h)."""
+    _check(load_library().pasm_debug_waits(ctx.handle, skip_mma, wait_limit), "pasm_debug_waits")
 
 
 def pasm_tiles(ctx: Context, level: int):

@@ -224,7 +224,8 @@ cudaError_t proj_tc_prepare();
 // B0, B1, C0, C1 are K x ldk and m x ldk row-major.  err counts bounded waits
 // that gave up (the affected chunk then adds nothing to its tile).
 void proj_tc(const Launch& L, const SplitMat& A, const double* B0, const double* B1, double* C0, double* C1,
-             int ldk, int ncols, unsigned long long* hl, unsigned int* tickets, int* err);
+             int ldk, int ncols, unsigned long long* hl, unsigned int* tickets, int* err, int wait_limit = 0,
+             int skip_mma = 0);
 
 // *out = number of nonzero entries of active[0..k)
 void count_active(const Launch& L, const int* active, int k, int* out);

@@ -118,6 +118,8 @@ struct pasm_ctx {
   } nn;
   int capture_level = -1;        // residual capture for training data (pasm_nn_capture_residuals)
   float* capture_buf = nullptr;
+  // test hook of the projection's bounded completion wait (pasm_debug_waits)
+  int dbg_wait_limit = 0, dbg_skip_mma = 0;
   // float64-accurate coarse projections on the tensor cores: Q^T (b, c) and Q g
   bool proj_tc = false;
   SplitMat projQT, projQ;
@@ -190,15 +192,20 @@ int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32, bool spli
     if (h.nnz) CK(cudaMemcpy(d.v32, f.data(), sizeof(float) * (size_t)h.nnz, cudaMemcpyHostToDevice));
   }
   if (split_ff) {
-    // hi = nearest float, lo = nearest float of the remainder (about 48 bits)
+    // hi = nearest float, lo = nearest float of the remainder (about 48 bits).  A matrix whose
+    // low parts are all below 2^-48 of their high parts (float32 values, or values assembled with a
+    // few ulps of float64 rounding, as the constant-coefficient stiffness) is marked exact32 and its
+    // low parts are dropped: they lie below the double-float products' own rounding (2^-46).
     AL(c->allocs, &d.vff, (size_t)h.nnz);
     std::vector<float2> f((size_t)h.nnz);
     d.exact32 = true;
     for (int64_t q = 0; q < h.nnz; ++q) {
       const float hi = (float)h.val[q];
       f[(size_t)q] = make_float2(hi, (float)(h.val[q] - (double)hi));
-      if (f[(size_t)q].y != 0.f) d.exact32 = false;
+      if (!(std::fabs((double)f[(size_t)q].y) <= std::ldexp(std::fabs((double)hi), -48))) d.exact32 = false;
     }
+    if (d.exact32)
+      for (auto& v : f) v.y = 0.f;
     if (h.nnz) CK(cudaMemcpy(d.vff, f.data(), sizeof(float2) * (size_t)h.nnz, cudaMemcpyHostToDevice));
   }
   return PASM_OK;
@@ -420,7 +427,8 @@ struct PairState {
 // columns (tensor cores, float64-accurate, or float64 CUDA cores).
 void project_bc(pasm_ctx* c, const Launch& L, const double* b, const double* cc, double* bq, double* cq) {
   if (c->proj_tc) {
-    proj_tc(L, c->projQT, b, cc, bq, cq, c->ldk, 2 * c->ldk, c->proj_hl, c->proj_tickets, c->proj_err);
+    proj_tc(L, c->projQT, b, cc, bq, cq, c->ldk, 2 * c->ldk, c->proj_hl, c->proj_tickets, c->proj_err,
+            c->dbg_wait_limit, c->dbg_skip_mma);
   } else {
     dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, b, bq, c->ldk);
     dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, true, cc, cq, c->ldk);
@@ -464,7 +472,8 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   a.tol = ps.tol; a.score_norm = c->opts.score_norm; a.window = 3; a.diag = c->diag;
   secular_select(L, a);
   if (c->proj_tc)
-    proj_tc(L, c->projQ, c->g, nullptr, c->uH, nullptr, ldk, ldk, c->proj_hl, c->proj_tickets, c->proj_err);
+    proj_tc(L, c->projQ, c->g, nullptr, c->uH, nullptr, ldk, ldk, c->proj_hl, c->proj_tickets, c->proj_err,
+            c->dbg_wait_limit, c->dbg_skip_mma);
   else
     dense_mm<double>(L, c->NH, c->NH, c->Q, c->NH, false, c->g, c->uH, ldk);
   const double* w = c->uH;
@@ -711,7 +720,7 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
           float ah = 0.f, al = 0.f;
           if (q < qe && a.col[q] == m.col[p2]) {
             ah = (float)a.val[q];
-            al = (float)(a.val[q] - (double)ah);
+            al = v.A.exact32 ? 0.f : (float)(a.val[q] - (double)ah);   // as in A's own split values
             ++q;
           }
           am[(size_t)p2] = make_float4(ah, al, mh, (float)(m.val[p2] - (double)mh));
@@ -1254,6 +1263,15 @@ int pasm_project(pasm_ctx* c, const double* b, const double* cc, double* bq, dou
   CK(cudaMemcpyAsync(&after, c->proj_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
   CK(cudaStreamSynchronize(c->s));
   return after != before ? PASM_ETIMEOUT : PASM_OK;
+}
+
+int pasm_debug_waits(pasm_ctx* c, int skip_mma, int wait_limit) {
+  if (!c || wait_limit < 0) return PASM_EINVAL;
+  c->dbg_skip_mma = skip_mma ? 1 : 0;
+  c->dbg_wait_limit = wait_limit;
+  // a captured step graph holds the old launch arguments
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return PASM_OK;
 }
 
 int pasm_tiles(pasm_ctx* c, int level, int* chunks_per_thread) {

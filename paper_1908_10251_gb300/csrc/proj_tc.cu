@@ -86,10 +86,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Bounded wait for phase `parity` of an mbarrier; true when it completed.
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+// Bounded wait for phase `parity` of an mbarrier (at most `limit` polls); true when it completed.
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity, int limit) {
   uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it) {
+  for (int it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
         : "=r"(done)
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads)
     k_proj_tc(int m, int K, int Kpad, const uint16_t* __restrict__ planes, const int* __restrict__ rexp,
               const double* __restrict__ B0, const double* __restrict__ B1, double* __restrict__ C0,
               double* __restrict__ C1, int ldk, int ncols, unsigned long long* __restrict__ hl,
-              unsigned int* __restrict__ tickets, int* __restrict__ err) {
+              unsigned int* __restrict__ tickets, int* __restrict__ err, int wait_limit, int skip_mma) {
   constexpr DigitPlan P{};
   constexpr int S = kDigits, T = kDigitBits * kDigits;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -286,8 +286,12 @@ __global__ void __launch_bounds__(kThreads)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
   if (tid == 0) {
-    bool ok = wait_parity(bar_load, 0);
-    if (ok) {
+    bool ok = wait_parity(bar_load, 0, wait_limit);
+    // skip_mma (a test of the timeout path): no MMA is issued and nothing arrives on bar_mma, so
+    // its wait runs out with nothing in flight
+    if (ok && skip_mma) {
+      ok = wait_parity(bar_mma, 0, wait_limit);
+    } else if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t idesc =
           (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
@@ -306,10 +310,10 @@ __global__ void __launch_bounds__(kThreads)
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma));
-      ok = wait_parity(bar_mma, 0);
-      if (!ok) wait_parity(bar_mma, 0);  // MMAs still reading shared memory
+      ok = wait_parity(bar_mma, 0, wait_limit);
+      if (!ok) wait_parity(bar_mma, 0, kWaitLimit);  // MMAs still reading shared memory
     } else {
-      wait_parity(bar_load, 0);  // copies still in flight
+      wait_parity(bar_load, 0, kWaitLimit);  // copies still in flight
     }
     if (!ok) {
       atomicAdd(err, 1);
@@ -436,12 +440,13 @@ size_t proj_tickets(int m, int ncols_max) { return (size_t)((m + kM - 1) / kM) *
 cudaError_t proj_tc_prepare() { return allow_dynamic_smem((const void*)k_proj_tc, (size_t)kSmem); }
 
 void proj_tc(const Launch& L, const SplitMat& A, const double* B0, const double* B1, double* C0, double* C1,
-             int ldk, int ncols, unsigned long long* hl, unsigned int* tickets, int* err) {
+             int ldk, int ncols, unsigned long long* hl, unsigned int* tickets, int* err, int wait_limit,
+             int skip_mma) {
   dim3 grid((ncols + kN - 1) / kN, A.mtiles, (A.Kpad + kKC - 1) / kKC);
   const double m = A.m, K = A.K, n = ncols;
   L.begin(KC_PROJ, (m * K + K * n + m * n) * 8.0, 2.0 * m * K * n);
   k_proj_tc<<<grid, kThreads, kSmem, L.s>>>(A.m, A.K, A.Kpad, A.planes, A.rexp, B0, B1, C0, C1, ldk, ncols, hl,
-                                            tickets, err);
+                                            tickets, err, wait_limit > 0 ? wait_limit : kWaitLimit, skip_mma);
   L.bump();
 }
 

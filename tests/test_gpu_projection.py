@@ -146,3 +146,31 @@ def test_step_tensor_projection_matches_fp64_projection(pg):
     (l1, U1), (l2, U2) = res
     assert np.max(np.abs(l1 - l2) / l2) < 1e-13
     assert np.max(np.abs(U1 - U2)) / np.max(np.abs(U2)) < 1e-10
+
+
+def test_bounded_wait_runs_out_and_context_recovers(pg):
+    """The projection's MMA completion wait is bounded.  The test hook makes it
+    run out safely -- no MMA is issued, so nothing arrives on the mbarrier and
+    nothing is in flight when the CTA gives up and frees its TMEM: the call
+    reports PASM_ETIMEOUT.  With the hook reset, the same context projects
+    correctly again (the timed-out tiles still took part in the ticket
+    protocol, so the integer accumulators were left cleared)."""
+    ctx, Q = make_ctx(pg, 2, 32, 16, 16)
+    NH = Q.shape[0]
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal((NH, 16))
+    c = rng.standard_normal((NH, 16))
+    bq = np.zeros((NH, 16)); cq = np.zeros((NH, 16))
+    pg.pasm_debug_waits(ctx, 1, 64)
+    with pytest.raises(pg.PasmError) as ei:
+        pg.pasm_project(ctx, b, c, bq, cq)
+    assert ei.value.code == pg.PASM_ETIMEOUT
+    pg.pasm_debug_waits(ctx, 0, 0)
+    for _ in range(2):
+        pg.pasm_project(ctx, b, c, bq, cq)
+        check_against_exact(Q, b, bq, rng, samples=40)
+        check_against_exact(Q, c, cq, rng, samples=40)
+    # a whole correction step still runs on the context
+    pg.pasm_step(ctx)
+    with pytest.raises(pg.PasmError):
+        pg.pasm_debug_waits(ctx, 0, -1)
