@@ -1,6 +1,9 @@
 """Write the reference eigenvalue tables under tests/golden/ (calls only
 meshgen and oracle/).  Run: python tests/golden/make_golden.py [name ...]
 
+Run: python tests/golden/make_golden.py [name ...] [--procs=P]  (P processes
+split the pairs of an iteration history; pairs are independent.)
+
 Each table holds the smallest discrete eigenvalues of one synthetic workload
 (the P1 pencil of Section 2 on the named mesh), from oracle.reference
 (ARPACK shift-invert in 2D; in 3D, where the factorisation of the 2M-DoF
@@ -65,28 +68,66 @@ HISTORIES = {
 }
 
 
-def write_history(name):
-    """Eigenvalue iterates of the oracle's PASM (float64, coarse initial pairs,
-    two V-cycles per step) on one workload: one row per step, one column per
-    pair; pairs freeze once their relative change is below tol."""
-    import json
+def _history_chunk(args):
+    """The oracle's iteration for one chunk of pairs (pairs are independent,
+    Section 3.2): eigenvalue history and per-pair step counts."""
+    name, cols = args
     import oracle
     dim, N, Nc, k, tol, max_steps, nested = HISTORIES[name]
-    t = time.time()
     H = mg.build_hierarchy(dim, N, Nc)
     prob = oracle.Problem.from_hierarchy(H)
-    lam, U, steps, hist = oracle.solve(prob, k, tol=tol, max_steps=max_steps, history=True, nested=nested)
+    lam0, U0 = (oracle.pasm.initial_state_nested if nested else oracle.initial_state)(prob, k)
+    lam, U, steps, hist = oracle.solve(prob, len(cols), tol=tol, max_steps=max_steps, history=True,
+                                       lam0=lam0[cols], U0=U0[:, cols])
+    return cols, [list(map(float, row)) for row in hist], [int(v) for v in steps]
+
+
+def write_history(name, procs=1):
+    """Eigenvalue iterates of the oracle's PASM (float64, coarse initial pairs,
+    two V-cycles per step) on one workload: one row per step, one column per
+    pair; pairs freeze once their relative change is below tol.  With procs >
+    1 the pairs are split over that many processes (spawned)."""
+    import json
+    dim, N, Nc, k, tol, max_steps, nested = HISTORIES[name]
+    t = time.time()
+    procs = max(1, min(procs, k))
+    chunks = [list(range(k))[p::procs] for p in range(procs)]
+    if procs == 1:
+        outs = [_history_chunk((name, chunks[0]))]
+    else:
+        import multiprocessing as mp
+        # one BLAS thread per worker (the spawned interpreters read this when they import numpy)
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        os.environ["OMP_NUM_THREADS"] = "1"
+        with mp.get_context("spawn").Pool(procs) as pool:
+            outs = pool.map(_history_chunk, [(name, c) for c in chunks])
+    rows = max(len(h) for _, h, _ in outs)
+    hist = [[0.0] * k for _ in range(rows)]
+    steps = [0] * k
+    for cols, h, st in outs:
+        for r in range(rows):
+            row = h[min(r, len(h) - 1)]          # a chunk that stopped early keeps its last values
+            for j, c in enumerate(cols):
+                hist[r][c] = row[j]
+        for j, c in enumerate(cols):
+            steps[c] = st[j]
     out = {"dim": dim, "N_fine": N, "N_coarse": Nc, "k": k, "tol": tol, "max_steps": max_steps, "nested": nested,
-           "steps": [int(s) for s in steps], "history": [[float(v) for v in row] for row in hist],
-           "seconds": time.time() - t}
+           "steps": steps, "history": hist, "seconds": time.time() - t}
     with open(os.path.join(HERE, name + ".json"), "w") as f:
         json.dump(out, f)
     print(name, "%.1fs" % (time.time() - t), flush=True)
 
 
 if __name__ == "__main__":
-    for n in (sys.argv[1:] or list(TABLES) + list(HISTORIES)):
+    procs = 1
+    names = []
+    for a in sys.argv[1:]:
+        if a.startswith("--procs="):
+            procs = int(a.split("=")[1])
+        else:
+            names.append(a)
+    for n in (names or list(TABLES) + list(HISTORIES)):
         if n in HISTORIES:
-            write_history(n)
+            write_history(n, procs)
         else:
             write(n)
