@@ -580,3 +580,17 @@ def test_sine_transform_inverse_and_reference(dim, N):
     vals = smallest_eigenvalues_sine(dim, N, 6)
     dense = sla.eigh(A.toarray(), M.toarray(), eigvals_only=True)[:6]
     assert np.allclose(vals, dense, rtol=1e-12)
+
+
+def test_sine_inverse_keeps_the_low_modes_accurate():
+    """At h = 1/1024 the smallest stencil eigenvalue 2 - 2 cos(pi h) = 9.4e-6
+    loses ~7 digits when formed by subtraction; the inverse must hold the
+    lowest grid sine mode to full precision: A^{-1} applied to A v returns v
+    to 1e-14."""
+    from oracle.reference import laplacian_inverse
+    N = 1024
+    A, _ = mg.assemble(2, N)
+    t = np.arange(1, N) / N
+    v = np.kron(np.sin(np.pi * t), np.sin(np.pi * t))
+    back = laplacian_inverse(2, N)(A @ v)
+    assert np.abs(back - v).max() <= 1e-13 * np.abs(v).max()
