@@ -599,12 +599,13 @@ def run_e2e(pg, torch, H, S, precision):
     pg.pasm_solve(ctx, k, WORK["tol"], lam0.numpy(), U0.numpy(), lam.numpy(), U.numpy(), steps, status)  # warm
     torch.cuda.synchronize()
     times = []
-    for _ in range(3):     # median of three solves
+    for _ in range(5):     # median of five solves
         t0 = time.perf_counter()
         pg.pasm_solve(ctx, k, WORK["tol"], lam0.numpy(), U0.numpy(), lam.numpy(), U.numpy(), steps, status)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     dt = statistics.median(times)
+    log("end to end: solves %s ms" % ", ".join("%.1f" % (t * 1e3) for t in times))
     pg.pasm_destroy(ctx)
     nbytes_in = (n * k + k) * 8
     nbytes_out = (n * k + k) * 8 + 2 * k * 4

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -45,32 +46,52 @@ void drop_graph(pasm_batch* b) {
   b->in_graph.clear();
 }
 
-// Capture one correction step of every problem with active pairs into one graph.
+// Capture one correction step of every problem with active pairs into one graph.  The large
+// problems (block-vector work n_fine x k at least a quarter of the largest one's) run one after
+// another in one chain, largest first: their kernels are HBM-bound and gain nothing from sharing
+// the memory system, while two of them at once evict each other's rows from L2.  The small
+// problems run on their own branches beside the chain, so their launch-bound steps hide under it.
 int capture_step_graph(pasm_batch* b) {
   drop_graph(b);
   const int np = (int)b->ctx.size();
+  std::vector<int> members;
+  std::vector<double> work((size_t)np, 0.0);
+  double wmax = 0.0;
+  for (int p = 0; p < np; ++p) {
+    if (b->active[(size_t)p] <= 0) continue;
+    int64_t n = 0;
+    pasm_sizes(b->ctx[(size_t)p], &n, nullptr, nullptr, nullptr);
+    work[(size_t)p] = (double)n * b->k[(size_t)p];
+    wmax = std::max(wmax, work[(size_t)p]);
+    members.push_back(p);
+  }
+  std::vector<int> order = members;   // large ones first, by decreasing work
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[(size_t)a] > work[(size_t)c]; });
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(b->run, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return PASM_ECUDA;
   }
   int r = PASM_OK;
-  std::vector<int> members;
-  for (int p = 0; p < np && !r; ++p) {
-    if (b->active[(size_t)p] <= 0) continue;
+  int prev_large = -1;
+  for (int p : order) {
+    if (r) break;
+    const bool large = work[(size_t)p] >= 0.25 * wmax;
     // the context's own stream, where its step's kernels go
     cudaStream_t s = (cudaStream_t)pasm_ctx_stream(b->ctx[(size_t)p]);
-    if (cudaEventRecord(b->fork[(size_t)p], b->run) != cudaSuccess ||
-        cudaStreamWaitEvent(s, b->fork[(size_t)p], 0) != cudaSuccess) {
+    cudaEvent_t after = b->fork[(size_t)p];
+    if (cudaEventRecord(after, b->run) != cudaSuccess) { r = PASM_ECUDA; break; }
+    if (cudaStreamWaitEvent(s, after, 0) != cudaSuccess) { r = PASM_ECUDA; break; }
+    if (large && prev_large >= 0 && cudaStreamWaitEvent(s, b->join[(size_t)prev_large], 0) != cudaSuccess) {
       r = PASM_ECUDA;
       break;
     }
     r = pasm_ctx_enqueue_step(b->ctx[(size_t)p]);
-    if (!r && (cudaEventRecord(b->join[(size_t)p], s) != cudaSuccess ||
-               cudaStreamWaitEvent(b->run, b->join[(size_t)p], 0) != cudaSuccess))
-      r = PASM_ECUDA;
-    members.push_back(p);
+    if (!r && cudaEventRecord(b->join[(size_t)p], s) != cudaSuccess) r = PASM_ECUDA;
+    if (large) prev_large = p;
   }
+  for (int p : members)
+    if (!r && cudaStreamWaitEvent(b->run, b->join[(size_t)p], 0) != cudaSuccess) r = PASM_ECUDA;
   // end the capture in every case, so that no stream is left capturing
   const cudaError_t e = cudaStreamEndCapture(b->run, &g);
   if (!r && e != cudaSuccess) r = PASM_ECUDA;
