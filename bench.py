@@ -52,9 +52,9 @@ WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-13, "target": 1e-9,
           "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history",
           "stable_history": "cube_h128_H8_k32_nofreeze_history"}
 # the h = 1/2048 workload (4,190,209 DoF, H = 1/16, 8 grids, k = 128): its reference table holds the
-# 48 smallest eigenvalues, so only pairs 0..47 can be counted; no oracle history at this size
+# 136 smallest eigenvalues (every pair can be judged); no oracle history at this size
 WORK_H2048 = {"dim": 2, "N": 2048, "NH": 16, "k": 128, "tol": 1e-13, "target": 1e-9,
-         "golden": "square_h2048_k48", "history": None}
+         "golden": "square_h2048_k136", "history": None}
 # the small latency-bound workload: unit square h = 1/64 (3969 DoF), H = 1/8 (49), 4 grids, k = 8,
 # float64, pairs judged at 1e-10 (its stop rule is |d lambda| / lambda < 1e-10)
 WORK_C1 = {"dim": 2, "N": 64, "NH": 8, "k": 8, "tol": 1e-13, "target": 1e-10, "stop_tol": 1e-10,
@@ -911,6 +911,10 @@ def main_ours(args):
                             "steps_to_1e-9_eigenvalue_only": r["S_eig"],
                             "max_eig_err": (r["accuracy"] or {}).get("max_eig_err"),
                             "max_angle": (r["accuracy"] or {}).get("max_angle"),
+                            "missed_detail": {str(i): {"eig_err": r["accuracy"]["eig_err"][j],
+                                                       "angle": r["accuracy"]["angle"][j]}
+                                              for j, i in enumerate(r["accuracy"]["pairs"]) if i in r["missed"]}
+                            if r.get("accuracy") else None,
                             "learned_steps_accepted": r["accepted"],
                             **({"time_to_target_ms": r["S"] * r["ms_per_step"], "target": WORK_C1["target"],
                                 "solve_latency": r["latency"]} if "latency" in r else {})}

@@ -42,7 +42,8 @@ constexpr int kWaitLimit = 1 << 22;
 
 // conv: A operand [half][IR][IW][PB][8 channels] bf16; weights 9 x 512 B
 constexpr int kConvPlane = IR * IW * PB * 16;     // bytes of one channel half
-constexpr int kConvA = 2 * kConvPlane;
+constexpr int kConvHalf = kConvPlane + 64;        // distance of the two halves (bank offset)
+constexpr int kConvA = kConvHalf + kConvPlane;
 constexpr int kConvW = 9 * 512;
 constexpr int kConvSmem = kConvA + kConvW + 16;
 constexpr uint32_t kConvTmem = TR * 16;           // 128 columns
@@ -137,33 +138,27 @@ __global__ void __launch_bounds__(kThreads) k_tc_conv16(int nx, int ny, int ldk,
   if (warp == 0) tmem_alloc(tmem_slot, kConvTmem);
   for (int t = tid; t < kConvW / 16; t += kThreads)
     *reinterpret_cast<uint4*>(W + 16 * t) = __ldg(reinterpret_cast<const uint4*>(w2g) + t);
-  // input tile: thread item = (pixel, pair): its 16 channels (64 contiguous bytes, so a warp reads
-  // 2 KB in one sweep) -> two 16-byte rows of 8 bf16, one per channel half; consecutive threads
-  // store consecutive rows of one plane (no bank conflicts)
-#pragma unroll 2
-  for (int t = tid; t < IR * IW * PB; t += kThreads) {
-    const int q = t % PB, pix = t / PB;
+  // input tile: thread item = (pixel, pair, channel half): 8 floats (32 contiguous bytes; two
+  // consecutive threads read the two halves of one (pixel, pair)) -> 8 bf16, one 16-byte row of
+  // the half's plane.  The planes are kConvPlane + 64 bytes apart, so the two halves that one
+  // group of 8 threads stores fall on different banks.
+  for (int t = tid; t < IR * IW * PB * 2; t += kThreads) {
+    const int half = t & 1, pp = t >> 1;
+    const int q = pp % PB, pix = pp / PB;
     const int col = pix % IW, row = pix / IW;
     const int x = x0 - 1 + col, y = y0 - 1 + row, c = c0 + q;
-    float4 u[4];
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (x >= 0 && x < nx && y >= 0 && y < ny && c < k) {
-      const float4* src = reinterpret_cast<const float4*>(in + (((int64_t)y * nx + x) * ldk + c) * 16);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) u[i] = __ldg(src + i);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) u[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4* src = reinterpret_cast<const float4*>(in + (((int64_t)y * nx + x) * ldk + c) * 16 + half * 8);
+      a = __ldg(src);
+      b = __ldg(src + 1);
     }
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const float4 a = u[2 * half], b = u[2 * half + 1];
-      __align__(16) __nv_bfloat162 v[4];
-      v[0] = __floats2bfloat162_rn(tf<MODE>(a.x), tf<MODE>(a.y));
-      v[1] = __floats2bfloat162_rn(tf<MODE>(a.z), tf<MODE>(a.w));
-      v[2] = __floats2bfloat162_rn(tf<MODE>(b.x), tf<MODE>(b.y));
-      v[3] = __floats2bfloat162_rn(tf<MODE>(b.z), tf<MODE>(b.w));
-      *reinterpret_cast<uint4*>(A + half * kConvPlane + t * 16) = *reinterpret_cast<uint4*>(v);
-    }
+    __align__(16) __nv_bfloat162 v[4];
+    v[0] = __floats2bfloat162_rn(tf<MODE>(a.x), tf<MODE>(a.y));
+    v[1] = __floats2bfloat162_rn(tf<MODE>(a.z), tf<MODE>(a.w));
+    v[2] = __floats2bfloat162_rn(tf<MODE>(b.x), tf<MODE>(b.y));
+    v[3] = __floats2bfloat162_rn(tf<MODE>(b.z), tf<MODE>(b.w));
+    *reinterpret_cast<uint4*>(A + half * kConvHalf + pp * 16) = *reinterpret_cast<uint4*>(v);
   }
   asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -171,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_tc_conv16(int nx, int ny, int ldk,
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
   if (tid == 0) {
-    const uint64_t a0 = smem_desc(smem_u32(A), kConvPlane, PB * 16);
+    const uint64_t a0 = smem_desc(smem_u32(A), kConvHalf, PB * 16);
     const uint64_t b0 = smem_desc(smem_u32(W), 128, 256);
     for (int i = 0; i < TR; ++i) {
       const uint64_t ai = a0 + (uint64_t)((i * IW * PB * 16) >> 4);

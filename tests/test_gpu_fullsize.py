@@ -270,12 +270,15 @@ def test_h2048_k128_fp64_step_sampled_oracle_parity(pg, square2048):
 def test_h2048_k128_mixed_final_state(pg, square2048):
     """Mixed precision on the h = 1/2048, k = 128 workload, 40 steps, pairs
     frozen at |d lambda| / lambda < 1e-13: no eigenvalue ever drops below the
-    smallest reference eigenvalue (Ritz values are upper bounds); at the end the simple first
-    eigenvalue and the (1,2)/(2,1) cluster are within 1e-9 of the reference
-    table (the 48 smallest eigenvalues, LOBPCG), as are at least ten of the 48
-    pairs it covers, and every pair within 1e-9 is distinct in its cluster and
-    within an M-principal angle of 1e-6 of the reference eigenspace."""
-    ref_all = ga.golden_table("square_h2048_k48")
+    smallest reference eigenvalue (Ritz values are upper bounds); at the end
+    the simple first eigenvalue and the (1,2)/(2,1) cluster are within 1e-9 of
+    the reference table (the 136 smallest eigenvalues: ARPACK shift-invert with
+    the exact sine-transform inverse, agreeing with an independent LOBPCG
+    table of 48 values to 1.4e-14), as are at least ten of the 128 pairs, and
+    every pair within 1e-9 whose cluster the vector check covers is distinct
+    in its cluster and within an M-principal angle of 1e-6 of the reference
+    eigenspace."""
+    ref_all = ga.golden_table("square_h2048_k136")
     H = square2048
     k = 128
     ctx = setup_ctx(pg, H, precision=1)
@@ -288,12 +291,12 @@ def test_h2048_k128_mixed_final_state(pg, square2048):
     U = np.zeros((H.fine.n, k))
     pg.pasm_get(ctx, lam, U)
     pg.pasm_destroy(ctx)
-    err = acc.cluster_errors(lam[:len(ref_all)], ref_all)
+    err = acc.cluster_errors(lam, ref_all)
     within = np.where(err <= 1e-9)[0]
     assert np.all(err[:3] <= 1e-9), err[:3]
     assert len(within) >= 10, err
-    # the clusters of the pairs within 1e-9 whose eigenspace the table closes
+    # reference vectors up to the 48th eigenvalue (ARPACK at 4.2M DoF is costly beyond)
     cid = acc.clusters(ref_all)
-    closed = [int(i) for i in within if np.where(cid == cid[i])[0].max() + 1 < len(ref_all)]
+    closed = [int(i) for i in within if np.where(cid == cid[i])[0].max() + 1 < 42]
     vecs = ga.reference_vectors(H, 2, 2048, ref_all, max(closed))
-    ga.check_final(H.fine.M, lam, U[:, :], ref_all, vecs, closed)
+    ga.check_final(H.fine.M, lam, U, ref_all, vecs, closed)
