@@ -79,6 +79,8 @@ enum {
   PASM_TILE_CHAIN_R,            /* restriction chain of A u~, M u~                   */
   PASM_TILE_CHAIN_P,            /* prolongation chain of u_H                         */
   PASM_TILE_UPDATE,             /* u = alpha u~ + P_c u_H                            */
+  PASM_TILE_PROLONG_SWEEP,      /* prolongation fused with the first post-smoothing
+                                   sweep (float32 cycles)                            */
   PASM_TILE_N
 };
 
@@ -213,10 +215,11 @@ int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, do
 /* The tile shapes in use on `level`: chunks_per_thread[PASM_TILE_N] receives,
  * per kernel kind, the 16-byte chunks of a block-vector row each thread
  * handles (0 = the default shape: one chunk, or as many as keep at most 32
- * threads per row).  For PASM_TILE_JACOBI2_ZERO and PASM_TILE_RESID_RESTRICT,
- * -1 means the autotuner timed the fused kernel slower than its unfused pair
- * (one sweep from zero + one sweep; residual + restriction) on this level,
- * which then runs instead.  Errors: PASM_EINVAL. */
+ * threads per row).  For PASM_TILE_JACOBI2_ZERO, PASM_TILE_RESID_RESTRICT and
+ * PASM_TILE_PROLONG_SWEEP, -1 means the autotuner timed the fused kernel
+ * slower than its unfused pair (one sweep from zero + one sweep; residual +
+ * restriction; prolongation + sweep) on this level, which then runs instead.
+ * Errors: PASM_EINVAL. */
 int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 
 /* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else

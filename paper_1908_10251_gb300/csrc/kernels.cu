@@ -174,6 +174,96 @@ template void rowop<float>(const Launch&, RowOp, const DCsr&, const float*, cons
                            const float*, float, float*, int);
 
 // ----------------------------------------------------------------------------------------------
+// Prolongate-and-correct fused with the first post-smoothing sweep (float32 cycles):
+//   out = xn + omega D^{-1} (F - A xn),  xn = X + P Ec,
+// with xn formed on the fly for the row and each neighbour the sweep gathers (Ec, the coarse
+// correction, is a quarter of the rows and stays in L2), so the corrected iterate is never written
+// and read back.  Every product and sum is taken in the order of the unfused pair (the
+// prolongation's row sum of P Ec, then X + it; the sweep's row sum over A in CSR order).
+template <int CH>
+__global__ void __launch_bounds__(kBlock) k_prolong_jacobi(int n, const int* __restrict__ arp,
+                                                           const int* __restrict__ aci, const float* __restrict__ av,
+                                                           const int* __restrict__ prp, const int* __restrict__ pci,
+                                                           const float* __restrict__ pv, const float* __restrict__ X,
+                                                           const float* __restrict__ Ec, const float* __restrict__ F,
+                                                           const float* __restrict__ dinv, float omega,
+                                                           float* __restrict__ out, int ldk, int tpr) {
+  constexpr int V = 4;
+  const int rpb = kBlock / tpr;
+  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
+  const int lane = threadIdx.x % tpr;
+  if (row >= n) return;
+  const size_t base = (size_t)row * ldk;
+  float y[CH][V], z[CH][V], acc[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    Vec16<float>::load(F + base + (c * tpr + lane) * V, y[c]);
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[c][v] = z[c][v] = 0.f;
+  }
+  const float w = omega * dinv[row];
+  const int p1 = __ldg(arp + row + 1);
+  for (int p = __ldg(arp + row); p < p1; ++p) {
+    const int j = __ldg(aci + p);
+    const float a = __ldg(av + p);
+    float xn[CH][V], ap[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      ldg16<float>(X + (size_t)j * ldk + (c * tpr + lane) * V, xn[c]);
+#pragma unroll
+      for (int v = 0; v < V; ++v) ap[c][v] = 0.f;
+    }
+    const int q1 = __ldg(prp + j + 1);
+    for (int q = __ldg(prp + j); q < q1; ++q) {
+      const int m = __ldg(pci + q);
+      const float pw = __ldg(pv + q);
+      float e[CH][V];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) ldg16<float>(Ec + (size_t)m * ldk + (c * tpr + lane) * V, e[c]);
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int v = 0; v < V; ++v) ap[c][v] = fmaf(pw, e[c][v], ap[c][v]);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const float x = xn[c][v] + ap[c][v];
+        if (j == row) z[c][v] = x;
+        acc[c][v] = fmaf(a, x, acc[c][v]);
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    float r[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) r[v] = fmaf(w, y[c][v] - acc[c][v], z[c][v]);
+    Vec16<float>::store(out + base + (c * tpr + lane) * V, r);
+  }
+}
+
+void prolong_jacobi(const Launch& L, const DCsr& A, const DCsr& P, const float* X, const float* Ec, const float* F,
+                    const float* dinv, float omega, float* out, int ldk) {
+  if (A.n_rows == 0) return;
+  Geo g = geometry<float>(ldk, L.geo);
+  const int rpb = kBlock / g.tpr;
+  const int grid = (A.n_rows + rpb - 1) / rpb;
+  {
+    const double rows = A.n_rows, nnz = (double)A.nnz, pnnz = (double)P.nnz;
+    // the matrices, X gathered once, Ec (P's columns) once, F read, out written, D^{-1}
+    const double bytes = (nnz + pnnz) * 8.0 + 2 * (rows + 1) * 4.0 + 3.0 * rows * ldk * 4.0 +
+                         P.n_cols * (double)ldk * 4.0 + rows * 4.0;
+    L.rows(A.n_rows);
+    L.begin(KC_JACOBI, bytes, 2.0 * (nnz + pnnz) * ldk + 4.0 * rows * ldk);
+  }
+  PASM_DISPATCH_CH(g.ch, k_prolong_jacobi<CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v32, P.rp, P.ci,
+                                                                          P.v32, X, Ec, F, dinv, omega, out, ldk,
+                                                                          g.tpr));
+  L.bump();
+}
+
+// ----------------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_jacobi_zero(int64_t total, int ldk, const T* __restrict__ dinv, T omega, const T* __restrict__ F,
                               T* __restrict__ out) {

@@ -70,6 +70,10 @@ enum RowOp { OP_JACOBI = 0, OP_RESID = 1, OP_SPMM = 2, OP_SPMM_ADD = 3 };
 template <typename T>
 void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, const T* Z, const T* dinv,
            T omega, T* out, int ldk);
+// out = xn + omega D^{-1} (F - A xn), xn = X + P Ec (prolongation fused with the first float32
+// post-smoothing sweep; the operations of rowop(OP_SPMM_ADD) then rowop(OP_JACOBI), in their order)
+void prolong_jacobi(const Launch& L, const DCsr& A, const DCsr& P, const float* X, const float* Ec, const float* F,
+                    const float* dinv, float omega, float* out, int ldk);
 
 // out = omega * dinv .* F  (first Jacobi sweep from a zero guess)
 template <typename T>

@@ -353,14 +353,26 @@ T* vcycle(pasm_ctx* c, int l, const TopOut* top = nullptr) {
              (T*)c->lv[l - 1].vF, ldk);
   }
   T* ec = vcycle<T>(c, l - 1);
-  rowop<T>(launcher(c, l, PASM_TILE_PROLONG), OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
+  // float32 Jacobi post-smoothing: the prolongation and the first sweep in one kernel, unless the
+  // autotuner timed the pair faster, the first sweep is the top level's fused last sweep, or the
+  // level runs the learned step or captures training data before its first sweep
+  const bool fuse_ps = Fused<T>::on && !cg && c->geo[(size_t)l][PASM_TILE_PROLONG_SWEEP] >= 0 &&
+                       (c->opts.nu_post >= 2 || (c->opts.nu_post == 1 && !top)) && c->capture_level != l &&
+                       !(c->opts.smoother == PASM_LEARNED && c->nn.ready && c->nn.nx[(size_t)l] != 0);
+  if (fuse_ps) {
+    prolong_jacobi(launcher(c, l, PASM_TILE_PROLONG_SWEEP), v.A, v.P, (const float*)cur, (const float*)ec,
+                   (const float*)F, v.dinv32, (float)om, (float*)tmp, ldk);
+    std::swap(cur, tmp);
+  } else {
+    rowop<T>(launcher(c, l, PASM_TILE_PROLONG), OP_SPMM_ADD, v.P, ec, cur, nullptr, nullptr, om, cur, ldk);
+  }
   if (cg) {
     cg_smooth<T>(L, v.A, F, cur, false, tmp, (T*)v.vP, (T*)v.vQ, c->cg, ldk, c->opts.nu_post);
     return cur;
   }
-  s = 0;
-  if (Fused<T>::on) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
-  if (s == 1) std::swap(cur, tmp);
+  s = fuse_ps ? 1 : 0;
+  if (Fused<T>::on && !fuse_ps) s = post_hooks(c, l, (float*)cur, (float*)tmp, (float*)F);
+  if (s == 1 && !fuse_ps) std::swap(cur, tmp);
   for (; s < c->opts.nu_post; ++s) {
     if (Fused<T>::on && top && s == c->opts.nu_post - 1) {
       // last sweep fused with the outer update; the cycle's result is in top->X
@@ -948,9 +960,13 @@ static int autotune(pasm_ctx* c) {
         rowop<float>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (float*)w.vF, ldk);
       });
       if (t_r + t_s < t_rr) c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] = -1;    // split: residual, then restriction
-      pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
+      const float t_p = pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
         rowop<float>(L, OP_SPMM_ADD, v.P, (float*)w.vE, E, nullptr, nullptr, om, E, ldk);
       });
+      const float t_ps = pick(l, PASM_TILE_PROLONG_SWEEP, c32, [&](const Launch& L) {
+        prolong_jacobi(L, v.A, v.P, E, (float*)w.vE, F, v.dinv32, om, Tm, ldk);
+      });
+      if (t_p + t_j < t_ps) c->geo[(size_t)l][PASM_TILE_PROLONG_SWEEP] = -1;   // split: prolongation, then sweep
       pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
         outer_rhs_residual_ff(L, v.A, v.M, c->lam, c->Uff, c->Fd, F, ldk);
       });
