@@ -711,7 +711,8 @@ def oracle_reach(hist, work):
 
 def reference_counts():
     """steps to 1e-9 and converged pairs of the oracle's own iteration on the
-    full workload (tests/golden, written by the oracle)."""
+    full workload (tests/golden, written by the oracle), over the reference
+    set (the pairs it reaches and, without freezing, still holds)."""
     p = os.path.join(ROOT, "tests", "golden", WORK["history"] + ".json")
     if not os.path.exists(p):
         return None
@@ -719,6 +720,9 @@ def reference_counts():
         d = json.load(f)
     ref_all = load_golden(WORK["golden"])
     reach = first_reach(np.array(d["history"]), ref_all[:WORK["k"]], WORK["target"], ref_all)
+    refset = reference_set(WORK)
+    if refset is not None:
+        reach = reach[refset]
     conv = int((reach >= 0).sum())
     return (int(reach.max()) if conv else len(d["history"]) - 1), conv
 
