@@ -356,6 +356,9 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
                 break
     conv = len(F)
     missed = [int(i) for i in pset if i not in F]
+    if F:
+        # the eigenvalue-only step count over the same counted pairs, for comparison with S
+        conv_eig, S_eig = time_to_target(reach, np.array(F), calib_steps)
     accuracy = {"step": S, "vector_checks": checks, "angle_max_allowed": ANGLE_MAX,
                 "pairs": [int(i) for i in pset], "counted": [int(i) for i in F],
                 "eig_err": [float(rep["err"][i]) for i in pset],

@@ -144,6 +144,63 @@ def apply(w, r_grid, bf16_layer2: bool = False):
     return conv(h, W3)[..., 0]
 
 
+def _gamma(n, u):
+    """n u / (1 - n u): the bound on the relative error of n rounded operations (Higham)."""
+    return n * u / (1.0 - n * u)
+
+
+def bf16_forward_bound(w, r_grid):
+    """Elementwise bound on |N~(r) - apply(w, r, bf16_layer2=True)|, where N~ is
+    any evaluation that computes layer 1 as 9 float32 FMAs per output in tap
+    order (dy, then dx), rounds relu(+-z1) of its own float32 z1 to bfloat16,
+    sums layer 2's exact products of those operands and of the bfloat16 W2 in
+    float32 (144 terms, any order, rounded or truncated), forms h in float32
+    and computes layer 3 as 144 float32 FMAs.  r is float32 on both sides.
+      z1: the running error of the FMA chain, e_i <= (1 + u) e_(i-1) + u |s_i|
+          with s_i the exact partial sums, gives |z1~ - z1| <= d1 =
+          (1 + 10^-6) 2^-24 sum_i |s_i| + gamma_9(2^-53) (|W1| * |r|) (the
+          second term: the oracle's own float64 z1);
+      a = bf16(relu(+-z1)): relu and round-to-nearest are monotone, so both
+          sides' a lie in [bf16(relu(+-z1 - d1)), bf16(relu(+-z1 + d1))]; the
+          width da of that interval is zero unless a rounding boundary lies
+          within d1 of +-z1, and then one bfloat16 step;
+      z2: |dz2| <= |W2b| * da + gamma_144(2^-23) (|W2b| * (|a| + da));
+      h = (relu(z2+) - relu(z2-)) / 2 (relu is 1-Lipschitz, one float32
+          subtraction): |dh| <= (|dz2+| + |dz2-|) / 2 + 2^-23 (|h| + that);
+      d: |dd| <= |W3| * dh + gamma_144(2^-24) (|W3| * (|h| + dh))
+              + gamma_144(2^-53) (|W3| * |h|) (the oracle's own rounding).
+    Returns the bound as images (B, ny, nx)."""
+    W1, W2, W3 = unpack(w)
+    u32, u64 = 2.0 ** -24, 2.0 ** -53
+    x = np.asarray(r_grid, dtype=np.float64)[..., None]
+    z1 = conv(x, W1)
+    B, ny, nx, _ = x.shape
+    xp = np.zeros((B, ny + 2, nx + 2, 1))
+    xp[:, 1:-1, 1:-1] = x
+    part, run = np.zeros(z1.shape), np.zeros(z1.shape)
+    for tap in range(9):
+        dy, dx = divmod(tap, 3)
+        part = part + xp[:, dy:dy + ny, dx:dx + nx] * W1[dy, dx, 0]
+        run += np.abs(part)
+    d1 = (1.0 + 1e-6) * u32 * run + 2.0 * _gamma(9, u64) * conv(np.abs(x), np.abs(W1))
+    W2b = np.abs(bf16(W2))
+    dz2, a_abs = [], []
+    for s in (1.0, -1.0):
+        lo = bf16(np.maximum(s * z1 - d1, 0.0))
+        hi = bf16(np.maximum(s * z1 + d1, 0.0))
+        da = hi - lo
+        a = bf16(np.maximum(s * z1, 0.0))
+        dz2.append(conv(da, W2b) + _gamma(144, 2.0 * u32) * conv(a + da, W2b))
+        a_abs.append(a)
+    z2p, z2m = conv(a_abs[0], bf16(W2)), conv(a_abs[1], bf16(W2))
+    h = 0.5 * (np.maximum(z2p, 0.0) - np.maximum(z2m, 0.0))
+    dh = 0.5 * (dz2[0] + dz2[1])
+    dh = dh + 2.0 * u32 * (np.abs(h) + dh)
+    W3a = np.abs(W3)
+    dd = conv(dh, W3a) + _gamma(144, u32) * conv(np.abs(h) + dh, W3a) + _gamma(144, u64) * conv(np.abs(h), W3a)
+    return dd[..., 0]
+
+
 def loss_and_grad(w, A, R, nx, ny):
     """L = mean_j |r_j - A N(r_j)|^2 / |r_j|^2 over the columns r_j of R (n, k)
     and its gradient with respect to the packed weights."""

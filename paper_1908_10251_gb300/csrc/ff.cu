@@ -197,6 +197,10 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
                        const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
                        const double* __restrict__ lam, const double* __restrict__ U, float2* __restrict__ Fd,
                        float* __restrict__ R, int ldk, int tpr) {
+  // the eigenvalues as (hi, lo) pairs, split once per block rather than once per entry
+  extern __shared__ float2 lsp[];  // [ldk]
+  for (int t = threadIdx.x; t < ldk; t += blockDim.x) ff_split(__ldg(lam + t), lsp[t].x, lsp[t].y);
+  __syncthreads();
   const int rpb = kBlock / tpr;
   const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
@@ -213,9 +217,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     float f[2][2], r[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      float lh, ll;
-      ff_split(__ldg(lam + col + v), lh, ll);
-      ff_mul(lh, ll, muh[c][v], mul[c][v], f[v][0], f[v][1]);
+      const float2 l = lsp[col + v];
+      ff_mul(l.x, l.y, muh[c][v], mul[c][v], f[v][0], f[v][1]);
       r[v] = __fadd_rn(__fsub_rn(f[v][0], auh[c][v]), __fsub_rn(f[v][1], aul[c][v]));
     }
     *reinterpret_cast<float4*>(Fd + base + col) = make_float4(f[0][0], f[0][1], f[1][0], f[1][1]);
@@ -372,6 +375,9 @@ __global__ void __launch_bounds__(kBlock)
                 const double* __restrict__ W, const double* __restrict__ X, const double* __restrict__ alpha,
                 const int* __restrict__ upd, double* __restrict__ U, double* __restrict__ Usplit, int ldk, int tpr,
                 int identity) {
+  extern __shared__ float2 asp[];  // [ldk]: alpha as (hi, lo) pairs, split once per block
+  for (int t = threadIdx.x; t < ldk; t += blockDim.x) ff_split(__ldg(alpha + t), asp[t].x, asp[t].y);
+  __syncthreads();
   const int rpb = kBlock / tpr;
   const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
@@ -395,11 +401,10 @@ __global__ void __launch_bounds__(kBlock)
     float h[2], l[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      float ah, al;
-      ff_split(__ldg(alpha + col + v), ah, al);
+      const float2 a = asp[col + v];
       h[v] = wh[c][v];
       l[v] = wl[c][v];
-      ff_mac(h[v], l[v], ah, al, xh[v], xl[v]);
+      ff_mac(h[v], l[v], a.x, a.y, xh[v], xl[v]);
       ff_norm(h[v], l[v]);
     }
     if (!U) {  // the state lives in pairs only: write the updated pairs, keep the frozen one
@@ -439,7 +444,7 @@ void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const 
     L.begin(KC_OUTER_RHS, nnz * 12.0 + 2 * (n + 1) * 4.0 + n * ldk * (16.0 + 4.0), 2.0 * nnz * ldk + 2.0 * n * ldk);
   }
 #define PASM_FF_RHS(AEX)                                                                      \
-  PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH, AEX><<<grid, kBlock, 0, L.s>>>(                \
+  PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH, AEX><<<grid, kBlock, ldk * sizeof(float2), L.s>>>( \
                              A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, lam, U,            \
                              reinterpret_cast<float2*>(Fd), R, ldk, g.tpr))
   if (A.exact32) { PASM_FF_RHS(true); } else { PASM_FF_RHS(false); }
@@ -558,7 +563,8 @@ void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, boo
   const float2* pv = P ? P->vff : nullptr;
   const bool ex = P ? P->exact32 : true;
 #define PASM_FF_UPD(WF, EXV)                                                                                  \
-  PASM_FF_DISPATCH(g.ch, k_update_ff<CH, WF, EXV><<<grid, kBlock, 0, L.s>>>(n, rp, ci, pv, W, X, alpha, upd, U, \
+  PASM_FF_DISPATCH(g.ch, k_update_ff<CH, WF, EXV><<<grid, kBlock, ldk * sizeof(float2), L.s>>>(                \
+                             n, rp, ci, pv, W, X, alpha, upd, U,                                                \
                                                                            Usplit, ldk, g.tpr, identity))
   if (w_ff) {
     if (ex) { PASM_FF_UPD(true, true); } else { PASM_FF_UPD(true, false); }

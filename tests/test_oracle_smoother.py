@@ -195,3 +195,95 @@ def test_bf16_gradient_within_first_order_bound():
     _, gb = sm.loss_and_grad_bf16(w, A, R, nx, ny)
     assert np.all(np.abs(gb - g) <= sm.bf16_gradient_bound(w, A, R, nx, ny))
     assert np.abs(gb - g).max() > 0
+
+
+def _f32_fma(a, b, c):
+    """float32 a*b + c with the product exact (float64) and one rounding of
+    the sum to float32 through float64 (double rounding: within half a float64
+    ulp of one float32 rounding)."""
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(np.float32)
+
+
+def _bf16_trunc(x):
+    """bfloat16 by truncation (a wrong rounding, for the planted-mistake check)."""
+    b = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).view(np.uint32) & np.uint32(0xFFFF0000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def float32_forward(w, r_grid, round_a=sm.bf16):
+    """An independent float32 evaluation of N(r) in the order the fused
+    tensor-core kernel uses: layer 1 as 9 FMAs per channel (taps row-major),
+    relu(+-z1) of the float32 z1 rounded to bfloat16, layer 2 as float32 sums
+    of the exact bfloat16 products, h in float32, layer 3 as 144 FMAs."""
+    W1, W2, W3 = (np.asarray(x, np.float32) for x in sm.unpack(w))
+    x = np.asarray(r_grid, np.float32)
+    B, ny, nx = x.shape
+
+    def pad(v):
+        out = np.zeros((B, ny + 2, nx + 2) + v.shape[3:], np.float32)
+        out[:, 1:-1, 1:-1] = v
+        return out
+
+    xp = pad(x)
+    z1 = np.zeros((B, ny, nx, 16), np.float32)
+    for tap in range(9):
+        dy, dx = divmod(tap, 3)
+        v = xp[:, dy:dy + ny, dx:dx + nx][..., None]
+        z1 = _f32_fma(W1[dy, dx, 0][None, None, None, :], v, z1)
+    W2b = sm.bf16(W2).astype(np.float32)
+    z2 = []
+    for s in (1.0, -1.0):
+        a = pad(round_a(np.maximum(s * z1, 0.0)).astype(np.float32))
+        acc = np.zeros((B, ny, nx, 16), np.float32)
+        for tap in range(9):
+            dy, dx = divmod(tap, 3)
+            for ci in range(16):
+                acc = acc + a[:, dy:dy + ny, dx:dx + nx, ci:ci + 1] * W2b[dy, dx, ci][None, None, None, :]
+        z2.append(acc)
+    h = np.float32(0.5) * (np.maximum(z2[0], np.float32(0)) - np.maximum(z2[1], np.float32(0)))
+    hp = pad(h)
+    d = np.zeros((B, ny, nx), np.float32)
+    for tap in range(9):
+        dy, dx = divmod(tap, 3)
+        for c in range(16):
+            d = _f32_fma(W3[dy, dx, c, 0], hp[:, dy:dy + ny, dx:dx + nx, c], d)
+    return d.astype(np.float64)
+
+
+def _bound_case(seed, scale=2.0, n=23, B=4):
+    w = sm.init_weights(seed).astype(np.float32).astype(np.float64) * scale
+    r = np.random.default_rng(seed + 10).standard_normal((B, n, n)).astype(np.float32).astype(np.float64)
+    return w, r
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bf16_forward_bound_holds_for_a_float32_evaluation(seed):
+    """The derived elementwise bound covers an independent float32 evaluation
+    in the kernel's order, including outputs where the float32 z1 and the
+    float64 z1 round relu(+-z1) to different bfloat16 neighbours."""
+    w, r = _bound_case(seed)
+    ref = sm.apply(w, r, bf16_layer2=True)
+    got = float32_forward(w, r)
+    bound = sm.bf16_forward_bound(w, r)
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / bound)
+
+
+def test_bf16_forward_bound_is_below_a_bfloat16_step():
+    """Only the operands whose rounding boundary lies within the float32 error
+    of z1 (about 1e-4 of them) contribute a bfloat16 step; elsewhere the bound
+    is the worst-case float32 accumulation error, so the median output's bound
+    stays below a quarter of a bfloat16 step of the largest output."""
+    w, r = _bound_case(0)
+    ref = sm.apply(w, r, bf16_layer2=True)
+    bound = sm.bf16_forward_bound(w, r)
+    assert np.median(bound) < 0.25 * 2.0 ** -8 * np.abs(ref).max()
+
+
+def test_bf16_forward_bound_catches_a_wrong_rounding():
+    """Planted mistake: relu(+-z1) truncated to bfloat16 instead of rounded to
+    nearest; most outputs leave the bound."""
+    w, r = _bound_case(0)
+    ref = sm.apply(w, r, bf16_layer2=True)
+    bad = float32_forward(w, r, round_a=_bf16_trunc)
+    bound = sm.bf16_forward_bound(w, r)
+    assert np.mean(np.abs(bad - ref) > bound) > 0.5
