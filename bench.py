@@ -292,6 +292,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
     pg.pasm_init(ctx, k, w["tol"]); torch.cuda.synchronize()
     tune_s = time.perf_counter() - t0
     tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
+    tile_rows = pg.pasm_tile_rows(ctx, len(H.levels) - 1)
     init_ms = 0.0
     if init:
         torch.cuda.synchronize()
@@ -408,7 +409,7 @@ def run_mode(pg, torch, H, ref, precision, steps, warmup, rank, calib_steps=60, 
             "S_eig": S_eig, "converged_eig": conv_eig, "accuracy": accuracy,
             "launches_per_step": launches, "trace": trace, "clocks": cs.summary(), "final_lam": hist[-1].tolist(),
             "fine_jacobi": fine_jacobi, "accepted": accepted, "init_ms": init_ms, "missed": missed,
-            "tiles": tiles, "first_init_s": tune_s, "fine_sweep_update": fine_sweep_update,
+            "tiles": tiles, "tile_rows": tile_rows, "first_init_s": tune_s, "fine_sweep_update": fine_sweep_update,
             "residual_max": res_max,
             "reached_outside_set": [int(i) for i in np.where(reach >= 0)[0]
                                     if refset is not None and i not in set(refset.tolist())]}
@@ -898,6 +899,7 @@ def main_ours(args):
                    "eigen_residual_max": main["residual_max"],
                    "l2": "inputs larger than L2 (536 MB block vectors)", "parallelism": "replicas",
                    "tiles_finest": {kk: v for kk, v in main["tiles"].items() if v},
+                   "rows_per_block_finest": {kk: v for kk, v in main["tile_rows"].items() if v},
                    "first_init_s": round(main["first_init_s"], 3)},
         "e2e": {"value": e2e_value, "unit": "eigenpairs/s", "h2d_bytes_per_step": bin_ // max(S, 1),
                 "d2h_bytes_per_step": bout // max(S, 1), "seconds": e2e_s,
@@ -1025,12 +1027,18 @@ def main_case(args):
     torch.cuda.synchronize()
     wall = (time.perf_counter() - t0) / max(args.case_steps, 1) * 1e3
     trace = pg.pasm_trace_step(ctx)
+    fine = H.levels[-1].n
+    finest = [(name, round(t * 1e3, 1)) for name, rows, t, b, f in pg.pasm_trace_launches(ctx) if rows == fine]
+    shapes = {lv: {"chunks": {kk: v for kk, v in pg.pasm_tiles(ctx, lv).items() if v},
+                   "rows": {kk: v for kk, v in pg.pasm_tile_rows(ctx, lv).items() if v}}
+              for lv in range(1, len(H.levels))}
     pg.pasm_destroy(ctx)
     print(json.dumps({"case": {"dim": dim, "N": N, "NH": NH, "k": k, "mode": args.mode,
                                "smoother": args.case_smoother, "train_iters": args.case_train},
                       "ms_per_step_wall": wall,
                       "classes": {name: {"ms": t, "launches": n, "GBps": by / max(t, 1e-9) / 1e6}
-                                  for name, (t, by, fl, n) in sorted(trace.items(), key=lambda kv: -kv[1][0])}}))
+                                  for name, (t, by, fl, n) in sorted(trace.items(), key=lambda kv: -kv[1][0])},
+                      "finest_launches_us": finest, "tile_shapes": shapes}))
 
 
 def main():

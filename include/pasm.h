@@ -222,6 +222,13 @@ int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, do
  * Errors: PASM_EINVAL. */
 int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 
+/* Row blocks per thread block in use on `level`: rows_per_block[PASM_TILE_N]
+ * receives, per kernel kind, how many consecutive row blocks (of 256 / threads
+ * per row rows) one thread block walks -- 1 or 4 as the autotuner timed the
+ * float32 and float64 row kernels (sweeps, residuals, transfers), 0 for kinds
+ * it does not choose this for, which take 1.  Errors: PASM_EINVAL. */
+int pasm_tile_rows(pasm_ctx* ctx, int level, int* rows_per_block);
+
 /* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else
  * PASM_PROJ_FP64. */
 int pasm_projection_kind(pasm_ctx* ctx, int* kind);

@@ -87,6 +87,7 @@ def load_library():
         "pasm_secular_stats": (I, [P, P]),
         "pasm_residuals": (I, [P, P]),
         "pasm_tiles": (I, [P, I, P]),
+        "pasm_tile_rows": (I, [P, I, P]),
         "pasm_debug_waits": (I, [P, I, I]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -237,6 +238,13 @@ def pasm_tiles(ctx: Context, level: int):
     """{kernel kind: 16-byte chunks per thread (0 = default)} on `level`."""
     out = np.zeros(PASM_TILE_N, dtype=np.int32)
     _check(load_library().pasm_tiles(ctx.handle, level, out.ctypes.data), "pasm_tiles")
+    return dict(zip(TILE_KINDS, (int(v) for v in out)))
+
+
+def pasm_tile_rows(ctx: Context, level: int):
+    """{kernel kind: row blocks per thread block (0 = not chosen, runs 1)} on `level`."""
+    out = np.zeros(PASM_TILE_N, dtype=np.int32)
+    _check(load_library().pasm_tile_rows(ctx.handle, level, out.ctypes.data), "pasm_tile_rows")
     return dict(zip(TILE_KINDS, (int(v) for v in out)))
 
 

@@ -95,16 +95,28 @@ __device__ __forceinline__ void gather_rows(const int* __restrict__ ci, const T*
 }
 
 // ----------------------------------------------------------------------------------------------
+// Row blocks per block: a block may walk `rpt` consecutive row blocks, so that fewer blocks are
+// launched and the neighbour rows one row block gathers are still in L1 for the next.  The
+// autotuner picks 1 or 4 per level and kernel kind; untuned launches take 1.
+static int rows_per_block(const Launch& L) { return L.rpt > 0 ? L.rpt : 1; }
+
+// Float32 row operations: registers capped so that 2048 threads fit an SM (one chunk per thread)
+// or 1024 (two chunks); wider chunks and float64 keep the compiler's choice.
+template <typename T, int CH> struct RowMinBlocks { static constexpr int v = 1; };
+template <> struct RowMinBlocks<float, 1> { static constexpr int v = 8; };
+template <> struct RowMinBlocks<float, 2> { static constexpr int v = 4; };
+
 // Generic row operation (Jacobi sweep, residual, SpMM, SpMM + add).
 template <typename T, int CH, int OP>
-__global__ void __launch_bounds__(kBlock) k_rowop(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+__global__ void __launch_bounds__(kBlock, (RowMinBlocks<T, CH>::v)) k_rowop(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                    const T* __restrict__ av, const T* __restrict__ X,
                                                    const T* Y, const T* Z, const T* __restrict__ dinv, T omega,
-                                                   T* out, int ldk, int tpr) {
+                                                   T* out, int ldk, int tpr, int rpt) {
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   T acc[CH][V];
 #pragma unroll
@@ -138,6 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_rowop(int n, const int* __restrict__
     }
     Vec16<T>::store(out + off, r);
   }
+  }
 }
 
 template <typename T>
@@ -146,7 +159,8 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
   if (S.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int grid = (S.n_rows + rpb - 1) / rpb;
+  const int rpt = rows_per_block(L);
+  const int grid = (S.n_rows + rpb * rpt - 1) / (rpb * rpt);
   const T* av = vals<T>(S);
   {
     const double sz = sizeof(T), rows = S.n_rows, cols = S.n_cols, nnz = (double)S.nnz;
@@ -161,10 +175,10 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
   }
   PASM_DISPATCH_CH(g.ch,
     switch (op) {
-      case OP_JACOBI: k_rowop<T, CH, OP_JACOBI><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
-      case OP_RESID: k_rowop<T, CH, OP_RESID><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
-      case OP_SPMM: k_rowop<T, CH, OP_SPMM><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
-      case OP_SPMM_ADD: k_rowop<T, CH, OP_SPMM_ADD><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr); break;
+      case OP_JACOBI: k_rowop<T, CH, OP_JACOBI><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr, rpt); break;
+      case OP_RESID: k_rowop<T, CH, OP_RESID><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr, rpt); break;
+      case OP_SPMM: k_rowop<T, CH, OP_SPMM><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr, rpt); break;
+      case OP_SPMM_ADD: k_rowop<T, CH, OP_SPMM_ADD><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, av, X, Y, Z, dinv, omega, out, ldk, g.tpr, rpt); break;
     });
   L.bump();
 }
@@ -312,11 +326,12 @@ template <typename T, int CH>
 __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_jacobi2_zero(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                           const T* __restrict__ av, const T* __restrict__ dinv,
                                                           T omega, const T* __restrict__ F, T* __restrict__ out,
-                                                          int ldk, int tpr, int prescaled) {
+                                                          int ldk, int tpr, int prescaled, int rpt) {
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   T acc[CH][V];
 #pragma unroll
@@ -338,6 +353,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_jacobi2_zero(i
     for (int v = 0; v < V; ++v) r[v] = w * (T(2) * f[c][v] - acc[c][v]);
     Vec16<T>::store(out + off, r);
   }
+  }
 }
 
 // Residual and restriction in one pass: fc = R (f - A e), the residual of each
@@ -348,11 +364,12 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_resid_restrict
                                                             const int* __restrict__ arp, const int* __restrict__ aci,
                                                             const T* __restrict__ av, const T* __restrict__ E,
                                                             const T* __restrict__ F, T* __restrict__ out, int ldk,
-                                                            int tpr) {
+                                                            int tpr, int rpt) {
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= nc) return;
   T acc[CH][V];
 #pragma unroll
@@ -379,6 +396,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_resid_restrict
   const size_t base = (size_t)row * ldk;
 #pragma unroll
   for (int c = 0; c < CH; ++c) Vec16<T>::store(out + base + (c * tpr + lane) * V, acc[c]);
+  }
 }
 
 template <typename T>
@@ -386,7 +404,8 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
   if (A.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int grid = (A.n_rows + rpb - 1) / rpb;
+  const int rpt = rows_per_block(L);
+  const int grid = (A.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double sz = sizeof(T), rows = A.n_rows, nnz = (double)A.nnz;
     L.rows(A.n_rows);
@@ -396,7 +415,7 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
   const T* ws = scaled_vals<T>(A);
   PASM_DISPATCH_CH(g.ch, k_jacobi2_zero<T, CH><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, ws ? ws : vals<T>(A),
                                                                           dinv, omega, F, out, ldk, g.tpr,
-                                                                          ws ? 1 : 0));
+                                                                          ws ? 1 : 0, rpt));
   L.bump();
 }
 
@@ -405,7 +424,8 @@ void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, c
   if (R.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int grid = (R.n_rows + rpb - 1) / rpb;
+  const int rpt = rows_per_block(L);
+  const int grid = (R.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double sz = sizeof(T), nf = A.n_rows, nc = R.n_rows;
     L.rows(A.n_rows);
@@ -414,7 +434,7 @@ void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, c
             2.0 * (double)(A.nnz + R.nnz) * ldk + nf * ldk);
   }
   PASM_DISPATCH_CH(g.ch, k_resid_restrict<T, CH><<<grid, kBlock, 0, L.s>>>(R.n_rows, R.rp, R.ci, vals<T>(R), A.rp,
-                                                                            A.ci, vals<T>(A), E, F, out, ldk, g.tpr));
+                                                                            A.ci, vals<T>(A), E, F, out, ldk, g.tpr, rpt));
   L.bump();
 }
 

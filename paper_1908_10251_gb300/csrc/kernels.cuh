@@ -52,6 +52,7 @@ struct Launch {
   int* counter = nullptr;
   Tracer* tr = nullptr;
   int geo = 0;  // row-group kernels: 16-byte chunks per thread (0 = default; set by the autotuner)
+  int rpt = 0;  // float32 row kernels: row blocks each block walks (0 = by size; set by the autotuner)
   void begin(int cls, double bytes, double flops) const { if (tr) tracer_begin(tr, s, cls, bytes, flops); }
   void rows(int n) const { if (tr) tracer_rows(tr, n); }
   void bump() const {

@@ -129,6 +129,7 @@ struct pasm_ctx {
   CgWork cg;                               // CG smoothing: partial sums and per-column scalars
   // autotuned row-group geometry per level and kernel kind (0 = default), for block width tuned_ldk
   std::vector<std::array<int, PASM_TILE_N>> geo;
+  std::vector<std::array<int, PASM_TILE_N>> rpt;   // row blocks per block (0 = by size)
   int tuned_ldk = 0;
   int launches = 0;
   int last_launches = 0;
@@ -257,7 +258,10 @@ Launch launcher(pasm_ctx* c) {
 // launcher with the autotuned geometry of kernel kind `kind` on level l
 Launch launcher(pasm_ctx* c, int l, int kind) {
   Launch L = launcher(c);
-  if (l >= 0 && l < (int)c->geo.size()) L.geo = c->geo[(size_t)l][(size_t)kind];
+  if (l >= 0 && l < (int)c->geo.size()) {
+    L.geo = c->geo[(size_t)l][(size_t)kind];
+    L.rpt = c->rpt[(size_t)l][(size_t)kind];
+  }
   return L;
 }
 
@@ -709,6 +713,7 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
   c->nlev = n_levels;
   c->lv.resize((size_t)n_levels);
   c->geo.assign((size_t)n_levels, std::array<int, PASM_TILE_N>{});
+  c->rpt.assign((size_t)n_levels, std::array<int, PASM_TILE_N>{});
   const bool mixed = c->opts.precision == PASM_MIXED;
   for (int l = 0; l < n_levels; ++l) c->lv[(size_t)l].n = A[l].n_rows;
   for (int l = 0; l < n_levels; ++l) {
@@ -898,10 +903,11 @@ extern "C++" {
 static constexpr int kTuneRows = 16384;
 
 template <typename Fn>
-static float time_launch(pasm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int geo, Fn&& fn) {
+static float time_launch(pasm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int geo, Fn&& fn, int rpt = 0) {
   Launch L;
   L.s = c->s;
   L.geo = geo;
+  L.rpt = rpt;
   fn(L);
   cudaEventRecord(e0, c->s);
   for (int q = 0; q < 3; ++q) fn(L);
@@ -915,6 +921,7 @@ static float time_launch(pasm_ctx* c, cudaEvent_t e0, cudaEvent_t e1, int geo, F
 static int autotune(pasm_ctx* c) {
   if (!c->opts.autotune || c->tuned_ldk == c->ldk) return PASM_OK;
   for (auto& g : c->geo) g.fill(0);
+  for (auto& g : c->rpt) g.fill(0);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
@@ -924,17 +931,22 @@ static int autotune(pasm_ctx* c) {
   const bool mixed = c->opts.precision == PASM_MIXED;
   const int ldk = c->ldk;
   CK(cudaMemsetAsync(c->upd, 0, sizeof(int) * (size_t)ldk, c->s));
-  auto pick = [&](int l, int kind, int chunks, auto&& fn) -> float {
-    int best = 0;
+  // rows: the kernel kind also takes a number of row blocks per block (1 or 4)
+  auto pick = [&](int l, int kind, int chunks, auto&& fn, bool rows = false) -> float {
+    int best = 0, best_rpt = 0;
     float best_ms = 1e30f;
     for (int ch : {1, 2, 4, 8}) {
       if (chunks % ch != 0 || chunks / ch > 32) continue;
       // the bordering kernel keeps its per-block reduction within 48 KB of shared memory
       if (kind == PASM_TILE_BORDER && (size_t)(256 / (chunks / ch)) * 2 * ldk * sizeof(double) > 48 * 1024) continue;
-      const float ms = time_launch(c, e0, e1, ch, fn);
-      if (ms < best_ms) { best_ms = ms; best = ch; }
+      for (int r : {1, 4}) {
+        if (r > 1 && !rows) break;
+        const float ms = time_launch(c, e0, e1, ch, fn, rows ? r : 0);
+        if (ms < best_ms) { best_ms = ms; best = ch; best_rpt = rows ? r : 0; }
+      }
     }
     c->geo[(size_t)l][(size_t)kind] = best;
+    c->rpt[(size_t)l][(size_t)kind] = best_rpt;
     return best_ms;
   };
   const int c32 = ldk / 4, c64 = ldk / 2;  // 16-byte chunks per row: float32, float64 / pairs
@@ -946,23 +958,25 @@ static int autotune(pasm_ctx* c) {
       float *F = (float*)v.vF, *E = (float*)v.vE, *Tm = (float*)v.vT;
       const float om = (float)c->opts.omega;
       const float t_j2 = pick(l, PASM_TILE_JACOBI2_ZERO, c32,
-                              [&](const Launch& L) { jacobi2_zero<float>(L, v.A, v.dinv32, om, F, E, ldk); });
+                              [&](const Launch& L) { jacobi2_zero<float>(L, v.A, v.dinv32, om, F, E, ldk); }, true);
       const float t_j = pick(l, PASM_TILE_JACOBI, c32,
-                             [&](const Launch& L) { rowop<float>(L, OP_JACOBI, v.A, E, F, E, v.dinv32, om, Tm, ldk); });
+                             [&](const Launch& L) { rowop<float>(L, OP_JACOBI, v.A, E, F, E, v.dinv32, om, Tm, ldk); },
+                             true);
       const float t_j0 = time_launch(c, e0, e1, 0, [&](const Launch& L) { jacobi_zero<float>(L, v.n, v.dinv32, om, F, E, ldk); });
       if (t_j0 + t_j < t_j2) c->geo[(size_t)l][PASM_TILE_JACOBI2_ZERO] = -1;   // split: one sweep from zero + one sweep
       const float t_rr = pick(l, PASM_TILE_RESID_RESTRICT, c32,
-                              [&](const Launch& L) { resid_restrict<float>(L, v.R, v.A, E, F, (float*)w.vF, ldk); });
+                              [&](const Launch& L) { resid_restrict<float>(L, v.R, v.A, E, F, (float*)w.vF, ldk); },
+                              true);
       const float t_r = pick(l, PASM_TILE_RESID, c32, [&](const Launch& L) {
         rowop<float>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk);
-      });
+      }, true);
       const float t_s = pick(l, PASM_TILE_RESTRICT, c32, [&](const Launch& L) {
         rowop<float>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (float*)w.vF, ldk);
-      });
+      }, true);
       if (t_r + t_s < t_rr) c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] = -1;    // split: residual, then restriction
       const float t_p = pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
         rowop<float>(L, OP_SPMM_ADD, v.P, (float*)w.vE, E, nullptr, nullptr, om, E, ldk);
-      });
+      }, true);
       const float t_ps = pick(l, PASM_TILE_PROLONG_SWEEP, c32, [&](const Launch& L) {
         prolong_jacobi(L, v.A, v.P, E, (float*)w.vE, F, v.dinv32, om, Tm, ldk);
       });
@@ -988,15 +1002,16 @@ static int autotune(pasm_ctx* c) {
     } else {
       double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
       const double om = c->opts.omega;
-      pick(l, PASM_TILE_JACOBI, c64, [&](const Launch& L) { rowop<double>(L, OP_JACOBI, v.A, E, F, E, v.dinv64, om, Tm, ldk); });
+      pick(l, PASM_TILE_JACOBI, c64, [&](const Launch& L) { rowop<double>(L, OP_JACOBI, v.A, E, F, E, v.dinv64, om, Tm, ldk); },
+           true);
       pick(l, PASM_TILE_RESID, c64,
-           [&](const Launch& L) { rowop<double>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk); });
+           [&](const Launch& L) { rowop<double>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk); }, true);
       pick(l, PASM_TILE_RESTRICT, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (double*)w.vF, ldk);
-      });
+      }, true);
       pick(l, PASM_TILE_PROLONG, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM_ADD, v.P, (double*)w.vE, E, nullptr, nullptr, om, E, ldk);
-      });
+      }, true);
       pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
         outer_rhs_residual<double>(L, v.A, v.M, c->lam, c->U, c->Fd, F, ldk);
       });
@@ -1006,11 +1021,11 @@ static int autotune(pasm_ctx* c) {
       });
       pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM, v.R, c->YA, nullptr, nullptr, nullptr, 0.0, w.BA, ldk);
-      });
+      }, true);
       if (l < c->nlev - 1)
         pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) {
           rowop<double>(L, OP_SPMM, v.P, w.BA, nullptr, nullptr, nullptr, 0.0, v.BA, ldk);
-        });
+        }, true);
       const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
       pick(l, PASM_TILE_UPDATE, c64,
            [&](const Launch& L) { update_pairs(L, v.P, wsrc, c->X, c->alpha, c->upd, c->U, ldk); });
@@ -1293,6 +1308,12 @@ int pasm_debug_waits(pasm_ctx* c, int skip_mma, int wait_limit) {
 int pasm_tiles(pasm_ctx* c, int level, int* chunks_per_thread) {
   if (!c || !chunks_per_thread || level < 0 || level >= c->nlev) return PASM_EINVAL;
   for (int q = 0; q < PASM_TILE_N; ++q) chunks_per_thread[q] = c->geo[(size_t)level][(size_t)q];
+  return PASM_OK;
+}
+
+int pasm_tile_rows(pasm_ctx* c, int level, int* rows_per_block) {
+  if (!c || !rows_per_block || level < 0 || level >= c->nlev) return PASM_EINVAL;
+  for (int q = 0; q < PASM_TILE_N; ++q) rows_per_block[q] = c->rpt[(size_t)level][(size_t)q];
   return PASM_OK;
 }
 

@@ -43,9 +43,16 @@ def test_autotuned_tiles_match_default(pg, precision):
         tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
         assert all(v in (-1, 0, 1, 2, 4, 8) for v in tiles.values())
         assert all(v >= 0 for kk, v in tiles.items() if kk not in ("jacobi2_zero", "resid_restrict", "prolong_sweep"))
+        rows = pg.pasm_tile_rows(ctx, len(H.levels) - 1)
+        assert all(v in (0, 1, 4) for v in rows.values())
+        if tune:
+            assert rows["jacobi"] in (1, 4) and rows["prolong"] in (1, 4)   # row kernels: rows per block chosen
+            assert rows["border"] == 0 and rows["update"] == 0
         if not tune:
             assert all(v == 0 for v in tiles.values())
+            assert all(v == 0 for v in rows.values())
         assert all(v == 0 for v in pg.pasm_tiles(ctx, 1).values())   # 31 x 31: below the tuning size
+        assert all(v == 0 for v in pg.pasm_tile_rows(ctx, 1).values())
         for _ in range(3):
             pg.pasm_step(ctx)
         n = H.fine.n
