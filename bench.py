@@ -1011,11 +1011,22 @@ def main_case(args):
     H = mg.build_hierarchy(dim, N, NH)
     stream = torch.cuda.current_stream()
     smoother = {"jacobi": 0, "learned": 1, "cg": 2}[args.case_smoother]
-    opts = pg.pasm_default_opts(precision=0 if args.mode == "fp64" else 1, smoother=smoother)
+    # --case-tiles: the tile shapes a plain run saved (--case-tiles-save), so that a profiled run
+    # (whose launches the profiler slows unevenly) runs the shapes the autotuner picked unprofiled
+    opts = pg.pasm_default_opts(precision=0 if args.mode == "fp64" else 1, smoother=smoother,
+                                autotune=0 if args.case_tiles else 1)
     ctx = pg.pasm_setup([lv.A for lv in H.levels], [lv.M for lv in H.levels], H.P, opts, stream.cuda_stream)
+    if args.case_tiles:
+        with open(args.case_tiles) as f:
+            for lv, sh in json.load(f).items():
+                pg.pasm_set_tiles(ctx, int(lv), sh["chunks"], sh["rows"])
     if smoother == 1:
         pg.pasm_nn_setup(ctx, grid_widths(H), init_weights(0))   # cost does not depend on the weights
     pg.pasm_init(ctx, k, 0.0)
+    if args.case_tiles_save:
+        with open(args.case_tiles_save, "w") as f:
+            json.dump({lv: {"chunks": pg.pasm_tiles(ctx, lv), "rows": pg.pasm_tile_rows(ctx, lv)}
+                       for lv in range(len(H.levels))}, f)
     if args.case_train:
         lvl = len(H.levels) - 1
         R = np.random.default_rng(0).standard_normal((H.levels[lvl].n, k)).astype(np.float32)
@@ -1063,6 +1074,8 @@ def main():
     ap.add_argument("--case-steps", type=int, default=3)
     ap.add_argument("--case-smoother", default="jacobi", choices=["jacobi", "learned", "cg"])
     ap.add_argument("--case-train", type=int, default=0, help="Adam steps of the smoother before the case's steps")
+    ap.add_argument("--case-tiles-save", default=None, help="write the autotuned tile shapes of the case to this file")
+    ap.add_argument("--case-tiles", default=None, help="run the case with the tile shapes of this file (no autotuning)")
     args = ap.parse_args()
     if args.case:
         main_case(args)

@@ -229,6 +229,17 @@ int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
  * it does not choose this for, which take 1.  Errors: PASM_EINVAL. */
 int pasm_tile_rows(pasm_ctx* ctx, int level, int* rows_per_block);
 
+/* Set the tile shapes of `level` (a tuning cache: the values pasm_tiles and
+ * pasm_tile_rows returned for a context of the same hierarchy, block width and
+ * precision).  chunks_per_thread[PASM_TILE_N]: 0, 1, 2, 4 or 8, and -1 only for
+ * PASM_TILE_JACOBI2_ZERO, PASM_TILE_RESID_RESTRICT and PASM_TILE_PROLONG_SWEEP;
+ * rows_per_block[PASM_TILE_N] (NULL: all 0): 0, 1 or 4.  A shape that does not
+ * fit the block width runs the default shape.  The autotuner of a later
+ * pasm_init replaces them unless opts.autotune is 0 or the block width is the
+ * one already tuned.  Drops a captured step graph.  Errors: PASM_EINVAL (NULL
+ * chunks, bad level or value). */
+int pasm_set_tiles(pasm_ctx* ctx, int level, const int* chunks_per_thread, const int* rows_per_block);
+
 /* *kind = PASM_PROJ_TENSOR if the tensor-core projection is in use, else
  * PASM_PROJ_FP64. */
 int pasm_projection_kind(pasm_ctx* ctx, int* kind);

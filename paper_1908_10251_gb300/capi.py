@@ -88,6 +88,7 @@ def load_library():
         "pasm_residuals": (I, [P, P]),
         "pasm_tiles": (I, [P, I, P]),
         "pasm_tile_rows": (I, [P, I, P]),
+        "pasm_set_tiles": (I, [P, I, P, P]),
         "pasm_debug_waits": (I, [P, I, I]),
         "pasm_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -246,6 +247,15 @@ def pasm_tile_rows(ctx: Context, level: int):
     out = np.zeros(PASM_TILE_N, dtype=np.int32)
     _check(load_library().pasm_tile_rows(ctx.handle, level, out.ctypes.data), "pasm_tile_rows")
     return dict(zip(TILE_KINDS, (int(v) for v in out)))
+
+
+def pasm_set_tiles(ctx: Context, level: int, chunks: dict, rows: dict = None):
+    """Set the tile shapes of `level` from {kind: chunks per thread} and
+    {kind: row blocks per block} (kinds missing: 0), as pasm_tiles and
+    pasm_tile_rows return them."""
+    ch = np.array([int(chunks.get(kk, 0)) for kk in TILE_KINDS], dtype=np.int32)
+    rw = np.array([int((rows or {}).get(kk, 0)) for kk in TILE_KINDS], dtype=np.int32)
+    _check(load_library().pasm_set_tiles(ctx.handle, level, ch.ctypes.data, rw.ctypes.data), "pasm_set_tiles")
 
 
 def pasm_projection_kind(ctx: Context) -> int:

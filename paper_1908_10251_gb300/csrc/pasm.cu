@@ -1317,6 +1317,23 @@ int pasm_tile_rows(pasm_ctx* c, int level, int* rows_per_block) {
   return PASM_OK;
 }
 
+int pasm_set_tiles(pasm_ctx* c, int level, const int* chunks_per_thread, const int* rows_per_block) {
+  if (!c || !chunks_per_thread || level < 0 || level >= c->nlev) return PASM_EINVAL;
+  for (int q = 0; q < PASM_TILE_N; ++q) {
+    const int ch = chunks_per_thread[q], r = rows_per_block ? rows_per_block[q] : 0;
+    const bool fusable = q == PASM_TILE_JACOBI2_ZERO || q == PASM_TILE_RESID_RESTRICT || q == PASM_TILE_PROLONG_SWEEP;
+    if (!(ch == 0 || ch == 1 || ch == 2 || ch == 4 || ch == 8 || (ch == -1 && fusable))) return PASM_EINVAL;
+    if (!(r == 0 || r == 1 || r == 4)) return PASM_EINVAL;
+  }
+  for (int q = 0; q < PASM_TILE_N; ++q) {
+    c->geo[(size_t)level][(size_t)q] = chunks_per_thread[q];
+    c->rpt[(size_t)level][(size_t)q] = rows_per_block ? rows_per_block[q] : 0;
+  }
+  // a captured step graph holds the old launch shapes
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return PASM_OK;
+}
+
 int pasm_projection_kind(pasm_ctx* c, int* kind) {
   if (!c || !kind) return PASM_EINVAL;
   *kind = c->proj_tc ? PASM_PROJ_TENSOR : PASM_PROJ_FP64;

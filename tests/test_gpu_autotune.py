@@ -64,3 +64,44 @@ def test_autotuned_tiles_match_default(pg, precision):
     tl, tu = (1e-13, 1e-11) if precision == 0 else (1e-7, 1e-5)
     assert np.max(np.abs(l1 - l0) / l0) < tl
     assert np.max(np.abs(U1 - U0)) / np.max(np.abs(U0)) < tu
+
+
+def test_saved_tiles_reproduce_the_tuned_run(pg):
+    """A tuning cache: the shapes pasm_tiles / pasm_tile_rows report, set with
+    pasm_set_tiles on an untuned context of the same hierarchy, read back the
+    same and run the same kernels, so three steps agree bit for bit; values
+    outside the documented sets are rejected."""
+    H = mg.build_hierarchy(2, 256, 16)
+    A = [lv.A for lv in H.levels]
+    M = [lv.M for lv in H.levels]
+    runs = []
+    for tune in (1, 0):
+        opts = pg.pasm_default_opts(precision=1, autotune=tune)
+        ctx = pg.pasm_setup(A, M, H.P, opts, torch.cuda.current_stream().cuda_stream)
+        if not tune:
+            for lv, (ch, rw) in saved.items():
+                pg.pasm_set_tiles(ctx, lv, ch, rw)
+        pg.pasm_init(ctx, 32, 1e-12)
+        shapes = {lv: (pg.pasm_tiles(ctx, lv), pg.pasm_tile_rows(ctx, lv)) for lv in range(len(H.levels))}
+        if tune:
+            saved = shapes
+        else:
+            assert shapes == saved
+        for _ in range(3):
+            pg.pasm_step(ctx)
+        lam = np.zeros(32)
+        U = np.zeros((H.fine.n, 32))
+        pg.pasm_get(ctx, lam, U)
+        runs.append((lam, U))
+        if not tune:
+            bad = dict(saved[len(H.levels) - 1][0])
+            bad["jacobi"] = 3
+            with pytest.raises(RuntimeError):
+                pg.pasm_set_tiles(ctx, len(H.levels) - 1, bad)
+            bad = dict(saved[len(H.levels) - 1][0])
+            bad["border"] = -1
+            with pytest.raises(RuntimeError):
+                pg.pasm_set_tiles(ctx, len(H.levels) - 1, bad)
+            with pytest.raises(RuntimeError):
+                pg.pasm_set_tiles(ctx, len(H.levels) - 1, saved[len(H.levels) - 1][0], {"jacobi": 2})
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
