@@ -97,12 +97,16 @@ __device__ __forceinline__ void gather_rows(const int* __restrict__ ci, const T*
 // ----------------------------------------------------------------------------------------------
 // Row blocks per block: a block may walk `rpt` consecutive row blocks, so that fewer blocks are
 // launched and the neighbour rows one row block gathers are still in L1 for the next.  The
-// autotuner picks 1 or 4 per level and kernel kind; untuned launches take 1.
-static int rows_per_block(const Launch& L) { return L.rpt > 0 ? L.rpt : 1; }
+// autotuner picks 1 or 4 per level and kernel kind; untuned launches take 1.  Float32 kernels only:
+// for the float64 ones (bound by the float64 pipe) the count is the constant 1 on both sides.
+template <typename T> struct RowBlocks { __host__ __device__ static constexpr int of(int) { return 1; } };
+template <> struct RowBlocks<float> { __host__ __device__ static constexpr int of(int r) { return r; } };
+template <typename T>
+static int rows_per_block(const Launch& L) { return RowBlocks<T>::of(L.rpt > 0 ? L.rpt : 1); }
 
 // Float32 row operations: registers capped so that 2048 threads fit an SM (one chunk per thread)
 // or 1024 (two chunks); wider chunks and float64 keep the compiler's choice.
-template <typename T, int CH> struct RowMinBlocks { static constexpr int v = 1; };
+template <typename T, int CH> struct RowMinBlocks { static constexpr int v = 0; };  // 0: no minimum (compiler default)
 template <> struct RowMinBlocks<float, 1> { static constexpr int v = 8; };
 template <> struct RowMinBlocks<float, 2> { static constexpr int v = 4; };
 
@@ -115,8 +119,8 @@ __global__ void __launch_bounds__(kBlock, (RowMinBlocks<T, CH>::v)) k_rowop(int 
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
   const int lane = threadIdx.x % tpr;
-  for (int rr = 0; rr < rpt; ++rr) {
-  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
+  for (int rr = 0; rr < RowBlocks<T>::of(rpt); ++rr) {
+  const int row = (blockIdx.x * RowBlocks<T>::of(rpt) + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   T acc[CH][V];
 #pragma unroll
@@ -159,7 +163,7 @@ void rowop(const Launch& L, RowOp op, const DCsr& S, const T* X, const T* Y, con
   if (S.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int rpt = rows_per_block(L);
+  const int rpt = rows_per_block<T>(L);
   const int grid = (S.n_rows + rpb * rpt - 1) / (rpb * rpt);
   const T* av = vals<T>(S);
   {
@@ -330,8 +334,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_jacobi2_zero(i
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
   const int lane = threadIdx.x % tpr;
-  for (int rr = 0; rr < rpt; ++rr) {
-  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
+  for (int rr = 0; rr < RowBlocks<T>::of(rpt); ++rr) {
+  const int row = (blockIdx.x * RowBlocks<T>::of(rpt) + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   T acc[CH][V];
 #pragma unroll
@@ -368,8 +372,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<T>::gather) k_resid_restrict
   constexpr int V = Vec16<T>::N;
   const int rpb = kBlock / tpr;
   const int lane = threadIdx.x % tpr;
-  for (int rr = 0; rr < rpt; ++rr) {
-  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
+  for (int rr = 0; rr < RowBlocks<T>::of(rpt); ++rr) {
+  const int row = (blockIdx.x * RowBlocks<T>::of(rpt) + rr) * rpb + threadIdx.x / tpr;
   if (row >= nc) return;
   T acc[CH][V];
 #pragma unroll
@@ -404,7 +408,7 @@ void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const 
   if (A.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int rpt = rows_per_block(L);
+  const int rpt = rows_per_block<T>(L);
   const int grid = (A.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double sz = sizeof(T), rows = A.n_rows, nnz = (double)A.nnz;
@@ -424,7 +428,7 @@ void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, c
   if (R.n_rows == 0) return;
   Geo g = geometry<T>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int rpt = rows_per_block(L);
+  const int rpt = rows_per_block<T>(L);
   const int grid = (R.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double sz = sizeof(T), nf = A.n_rows, nc = R.n_rows;

@@ -1002,16 +1002,15 @@ static int autotune(pasm_ctx* c) {
     } else {
       double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
       const double om = c->opts.omega;
-      pick(l, PASM_TILE_JACOBI, c64, [&](const Launch& L) { rowop<double>(L, OP_JACOBI, v.A, E, F, E, v.dinv64, om, Tm, ldk); },
-           true);
+      pick(l, PASM_TILE_JACOBI, c64, [&](const Launch& L) { rowop<double>(L, OP_JACOBI, v.A, E, F, E, v.dinv64, om, Tm, ldk); });
       pick(l, PASM_TILE_RESID, c64,
-           [&](const Launch& L) { rowop<double>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk); }, true);
+           [&](const Launch& L) { rowop<double>(L, OP_RESID, v.A, E, F, nullptr, nullptr, om, Tm, ldk); });
       pick(l, PASM_TILE_RESTRICT, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (double*)w.vF, ldk);
-      }, true);
+      });
       pick(l, PASM_TILE_PROLONG, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM_ADD, v.P, (double*)w.vE, E, nullptr, nullptr, om, E, ldk);
-      }, true);
+      });
       pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
         outer_rhs_residual<double>(L, v.A, v.M, c->lam, c->U, c->Fd, F, ldk);
       });
@@ -1021,11 +1020,11 @@ static int autotune(pasm_ctx* c) {
       });
       pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) {
         rowop<double>(L, OP_SPMM, v.R, c->YA, nullptr, nullptr, nullptr, 0.0, w.BA, ldk);
-      }, true);
+      });
       if (l < c->nlev - 1)
         pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) {
           rowop<double>(L, OP_SPMM, v.P, w.BA, nullptr, nullptr, nullptr, 0.0, v.BA, ldk);
-        }, true);
+        });
       const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
       pick(l, PASM_TILE_UPDATE, c64,
            [&](const Launch& L) { update_pairs(L, v.P, wsrc, c->X, c->alpha, c->upd, c->U, ldk); });

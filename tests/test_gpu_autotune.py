@@ -45,9 +45,11 @@ def test_autotuned_tiles_match_default(pg, precision):
         assert all(v >= 0 for kk, v in tiles.items() if kk not in ("jacobi2_zero", "resid_restrict", "prolong_sweep"))
         rows = pg.pasm_tile_rows(ctx, len(H.levels) - 1)
         assert all(v in (0, 1, 4) for v in rows.values())
-        if tune:
-            assert rows["jacobi"] in (1, 4) and rows["prolong"] in (1, 4)   # row kernels: rows per block chosen
+        if tune and precision == 1:
+            assert rows["jacobi"] in (1, 4) and rows["prolong"] in (1, 4)   # float32 row kernels: chosen
             assert rows["border"] == 0 and rows["update"] == 0
+        if precision == 0:
+            assert all(v == 0 for v in rows.values())     # float64 row kernels walk one row block
         if not tune:
             assert all(v == 0 for v in tiles.values())
             assert all(v == 0 for v in rows.values())
