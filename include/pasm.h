@@ -225,9 +225,10 @@ int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 /* Row blocks per thread block in use on `level`: rows_per_block[PASM_TILE_N]
  * receives, per kernel kind, how many consecutive row blocks (of 256 / threads
  * per row rows) one thread block walks -- 1 or 4 as the autotuner timed the
- * float32 row kernels of the mixed-precision cycles (sweeps, residuals,
- * transfers), 0 for kinds it does not choose this for and in float64 mode
- * (these take 1).  Errors: PASM_EINVAL. */
+ * row kernels of the mixed-precision step (float32 sweeps, residuals and
+ * transfers; double-float outer residuals, transfer chains and update), 0 for
+ * kinds it does not choose this for and in float64 mode (these take 1).
+ * Errors: PASM_EINVAL. */
 int pasm_tile_rows(pasm_ctx* ctx, int level, int* rows_per_block);
 
 /* Set the tile shapes of `level` (a tuning cache: the values pasm_tiles and

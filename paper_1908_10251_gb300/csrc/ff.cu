@@ -45,6 +45,9 @@ Geo geometry_ff(int ldk, int pref) {
   return g;
 }
 
+// Row blocks one thread block walks (1 or 4, chosen by the autotuner; 1 when untuned).
+static int ff_rows(const Launch& L) { return L.rpt > 0 ? L.rpt : 1; }
+
 #define PASM_FF_DISPATCH(ch, ...)                          \
   switch (ch) {                                            \
     case 1: { constexpr int CH = 1; __VA_ARGS__; } break;  \
@@ -196,14 +199,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_rhs_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                        const int* __restrict__ mrp, const int* __restrict__ mci, const float2* __restrict__ mval,
                        const double* __restrict__ lam, const double* __restrict__ U, float2* __restrict__ Fd,
-                       float* __restrict__ R, int ldk, int tpr) {
+                       float* __restrict__ R, int ldk, int tpr, int rpt) {
   // the eigenvalues as (hi, lo) pairs, split once per block rather than once per entry
   extern __shared__ float2 lsp[];  // [ldk]
   for (int t = threadIdx.x; t < ldk; t += blockDim.x) ff_split(__ldg(lam + t), lsp[t].x, lsp[t].y);
   __syncthreads();
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   float muh[CH][2], mul[CH][2], auh[CH][2], aul[CH][2];
   // two separate gathers: the one-gather form (as in the bordering kernel) needs more registers
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     *reinterpret_cast<float4*>(Fd + base + col) = make_float4(f[0][0], f[0][1], f[1][0], f[1][1]);
     *reinterpret_cast<float2*>(R + base + col) = make_float2(r[0], r[1]);
   }
+  }
 }
 
 // R = Fd - A X as float32 (Fd and X as float pairs).
@@ -231,10 +236,11 @@ template <int CH, bool AEX>
 __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     k_outer_res_ff(int n, const int* __restrict__ arp, const int* __restrict__ aci, const float2* __restrict__ aval,
                    const float2* __restrict__ Fd, const double* __restrict__ X, float* __restrict__ R, int ldk,
-                   int tpr) {
+                   int tpr, int rpt) {
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   float axh[CH][2], axl[CH][2];
   gather_row_ff<CH, true, AEX>(arp, aci, aval, X, row, lane, tpr, ldk, axh, axl);
@@ -246,6 +252,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather)
     const float r0 = __fadd_rn(__fsub_rn(f.x, axh[c][0]), __fsub_rn(f.y, axl[c][0]));
     const float r1 = __fadd_rn(__fsub_rn(f.z, axh[c][1]), __fsub_rn(f.w, axl[c][1]));
     *reinterpret_cast<float2*>(R + base + col) = make_float2(r0, r1);
+  }
   }
 }
 
@@ -310,16 +317,18 @@ __global__ void __launch_bounds__(kBlock)
 template <int CH, bool FFIN, bool FFOUT, bool EX>
 __global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                                                      const float2* __restrict__ av, const double* __restrict__ X,
-                                                     double* __restrict__ out, int ldk, int tpr) {
+                                                     double* __restrict__ out, int ldk, int tpr, int rpt) {
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   float yh[CH][2], yl[CH][2];
   gather_row_ff<CH, FFIN, EX>(rp, ci, av, X, row, lane, tpr, ldk, yh, yl);
   const size_t base = (size_t)row * ldk;
 #pragma unroll
   for (int c = 0; c < CH; ++c) store_pair<FFOUT>(out, base + (c * tpr + lane) * 2, yh[c], yl[c]);
+  }
 }
 
 // X = B + E with E float32, X as float pairs; B as float pairs (may alias X)
@@ -374,13 +383,14 @@ __global__ void __launch_bounds__(kBlock)
     k_update_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float2* __restrict__ pv,
                 const double* __restrict__ W, const double* __restrict__ X, const double* __restrict__ alpha,
                 const int* __restrict__ upd, double* __restrict__ U, double* __restrict__ Usplit, int ldk, int tpr,
-                int identity) {
+                int identity, int rpt) {
   extern __shared__ float2 asp[];  // [ldk]: alpha as (hi, lo) pairs, split once per block
   for (int t = threadIdx.x; t < ldk; t += blockDim.x) ff_split(__ldg(alpha + t), asp[t].x, asp[t].y);
   __syncthreads();
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   float wh[CH][2], wl[CH][2];
   const size_t base = (size_t)row * ldk;
@@ -429,6 +439,7 @@ __global__ void __launch_bounds__(kBlock)
       store_pair<true>(Usplit, off, uh, ul);
     }
   }
+  }
 }
 
 }  // namespace
@@ -436,8 +447,8 @@ __global__ void __launch_bounds__(kBlock)
 void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const double* lam, const double* U,
                            double* Fd, float* R, int ldk) {
   const Geo g = geometry_ff(ldk, L.geo);
-  const int rpb = kBlock / g.tpr;
-  const int grid = (A.n_rows + rpb - 1) / rpb;
+  const int rpb = kBlock / g.tpr, rpt = ff_rows(L);
+  const int grid = (A.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double n = A.n_rows, nnz = (double)(A.nnz + M.nnz);
     L.rows(A.n_rows);
@@ -446,7 +457,7 @@ void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const 
 #define PASM_FF_RHS(AEX)                                                                      \
   PASM_FF_DISPATCH(g.ch, k_outer_rhs_res_ff<CH, AEX><<<grid, kBlock, ldk * sizeof(float2), L.s>>>( \
                              A.n_rows, A.rp, A.ci, A.vff, M.rp, M.ci, M.vff, lam, U,            \
-                             reinterpret_cast<float2*>(Fd), R, ldk, g.tpr))
+                             reinterpret_cast<float2*>(Fd), R, ldk, g.tpr, rpt))
   if (A.exact32) { PASM_FF_RHS(true); } else { PASM_FF_RHS(false); }
 #undef PASM_FF_RHS
   L.bump();
@@ -454,8 +465,8 @@ void outer_rhs_residual_ff(const Launch& L, const DCsr& A, const DCsr& M, const 
 
 void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const double* X, float* R, int ldk) {
   const Geo g = geometry_ff(ldk, L.geo);
-  const int rpb = kBlock / g.tpr;
-  const int grid = (A.n_rows + rpb - 1) / rpb;
+  const int rpb = kBlock / g.tpr, rpt = ff_rows(L);
+  const int grid = (A.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double n = A.n_rows, nnz = (double)A.nnz;
     L.rows(A.n_rows);
@@ -463,10 +474,10 @@ void outer_residual_ff(const Launch& L, const DCsr& A, const double* Fd, const d
   }
   if (A.exact32) {
     PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH, true><<<grid, kBlock, 0, L.s>>>(
-                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr, rpt));
   } else {
     PASM_FF_DISPATCH(g.ch, k_outer_res_ff<CH, false><<<grid, kBlock, 0, L.s>>>(
-                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr));
+                               A.n_rows, A.rp, A.ci, A.vff, reinterpret_cast<const float2*>(Fd), X, R, ldk, g.tpr, rpt));
   }
   L.bump();
 }
@@ -502,8 +513,8 @@ int border_products_ff(const Launch& L, const DCsr& A, const DCsr& M, const doub
 void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk) {
   if (S.n_rows == 0) return;
   const Geo g = geometry_ff(ldk, L.geo);
-  const int rpb = kBlock / g.tpr;
-  const int grid = (S.n_rows + rpb - 1) / rpb;
+  const int rpb = kBlock / g.tpr, rpt = ff_rows(L);
+  const int grid = (S.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double rows = S.n_rows, cols = S.n_cols, nnz = (double)S.nnz;
     L.rows(S.n_rows);
@@ -512,10 +523,10 @@ void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double*
 #define PASM_FF_SPMM(FI, FO)                                                                                   \
   if (S.exact32) {                                                                                             \
     PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO, true><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, X, \
-                                                                                  out, ldk, g.tpr));           \
+                                                                                  out, ldk, g.tpr, rpt));           \
   } else {                                                                                                     \
     PASM_FF_DISPATCH(g.ch, k_spmm_ff<CH, FI, FO, false><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, \
-                                                                                   X, out, ldk, g.tpr));       \
+                                                                                   X, out, ldk, g.tpr, rpt));       \
   }
   if (x_ff && out_ff) { PASM_FF_SPMM(true, true); }
   else if (x_ff) { PASM_FF_SPMM(true, false); }
@@ -550,8 +561,8 @@ void from_ff(const Launch& L, int64_t total, const double* in, double* out) {
 void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, bool w_ff, const double* X,
                      const double* alpha, const int* upd, double* U, double* Usplit, int ldk) {
   const Geo g = geometry_ff(ldk, L.geo);
-  const int rpb = kBlock / g.tpr;
-  const int grid = (n + rpb - 1) / rpb;
+  const int rpb = kBlock / g.tpr, rpt = ff_rows(L);
+  const int grid = (n + rpb * rpt - 1) / (rpb * rpt);
   const int identity = P ? 0 : 1;
   {
     const double nn = n, nnz = P ? (double)P->nnz : 0.0, cols = P ? (double)P->n_cols : nn;
@@ -565,7 +576,7 @@ void update_pairs_ff(const Launch& L, const DCsr* P, int n, const double* W, boo
 #define PASM_FF_UPD(WF, EXV)                                                                                  \
   PASM_FF_DISPATCH(g.ch, k_update_ff<CH, WF, EXV><<<grid, kBlock, ldk * sizeof(float2), L.s>>>(                \
                              n, rp, ci, pv, W, X, alpha, upd, U,                                                \
-                                                                           Usplit, ldk, g.tpr, identity))
+                                                                           Usplit, ldk, g.tpr, identity, rpt))
   if (w_ff) {
     if (ex) { PASM_FF_UPD(true, true); } else { PASM_FF_UPD(true, false); }
   } else {

@@ -983,21 +983,24 @@ static int autotune(pasm_ctx* c) {
       if (t_p + t_j < t_ps) c->geo[(size_t)l][PASM_TILE_PROLONG_SWEEP] = -1;   // split: prolongation, then sweep
       pick(l, PASM_TILE_OUTER_RHS, c64, [&](const Launch& L) {
         outer_rhs_residual_ff(L, v.A, v.M, c->lam, c->Uff, c->Fd, F, ldk);
-      });
-      pick(l, PASM_TILE_OUTER_RES, c64, [&](const Launch& L) { outer_residual_ff(L, v.A, c->Fd, c->X, F, ldk); });
+      }, true);
+      pick(l, PASM_TILE_OUTER_RES, c64, [&](const Launch& L) { outer_residual_ff(L, v.A, c->Fd, c->X, F, ldk); },
+           true);
       pick(l, PASM_TILE_BORDER, c64, [&](const Launch& L) {
         border_products_ff(L, v.A, v.M, c->X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
       });
-      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) { spmm_ff(L, v.R, c->YA, true, w.BA, l - 1 >= 1, ldk); });
+      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) { spmm_ff(L, v.R, c->YA, true, w.BA, l - 1 >= 1, ldk); },
+           true);
       if (l < c->nlev - 1)
-        pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); });
+        pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); },
+             true);
       const double* wsrc = (l - 1 >= 1) ? w.BA : c->uH;
       // the update skips frozen pairs, so it is timed with every pair selected, writing
       // into scratch (YM) instead of U
       CK(cudaMemsetAsync(c->upd, 1, sizeof(int) * (size_t)ldk, c->s));
       pick(l, PASM_TILE_UPDATE, c64, [&](const Launch& L) {
         update_pairs_ff(L, &v.P, v.n, wsrc, l - 1 >= 1, c->X, c->alpha, c->upd, c->YM, nullptr, ldk);
-      });
+      }, true);
       CK(cudaMemsetAsync(c->upd, 0, sizeof(int) * (size_t)ldk, c->s));
     } else {
       double *F = (double*)v.vF, *E = (double*)v.vE, *Tm = (double*)v.vT;
