@@ -52,9 +52,11 @@ WORK3D = {"dim": 3, "N": 128, "NH": 8, "k": 32, "tol": 1e-13, "target": 1e-9,
           "golden": "cube_h128_k40", "history": "cube_h128_H8_k32_history",
           "stable_history": "cube_h128_H8_k32_nofreeze_history"}
 # the h = 1/2048 workload (4,190,209 DoF, H = 1/16, 8 grids, k = 128): its reference table holds the
-# 136 smallest eigenvalues (every pair can be judged); no oracle history at this size
+# 136 smallest eigenvalues (every pair can be judged); the oracle's histories cover pairs 0..41 (the
+# higher ones do not converge with this coarse space), so its reference set is the stable pairs among them
 WORK_H2048 = {"dim": 2, "N": 2048, "NH": 16, "k": 128, "tol": 1e-13, "target": 1e-9,
-         "golden": "square_h2048_k136", "history": None}
+              "golden": "square_h2048_k136", "history": "square_h2048_H16_k42_history",
+              "stable_history": "square_h2048_H16_k42_nofreeze_history"}
 # the small latency-bound workload: unit square h = 1/64 (3969 DoF), H = 1/8 (49), 4 grids, k = 8,
 # float64, pairs judged at 1e-10 (its stop rule is |d lambda| / lambda < 1e-10)
 WORK_C1 = {"dim": 2, "N": 64, "NH": 8, "k": 8, "tol": 1e-13, "target": 1e-10, "stop_tol": 1e-10,

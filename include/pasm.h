@@ -81,6 +81,7 @@ enum {
   PASM_TILE_UPDATE,             /* u = alpha u~ + P_c u_H                            */
   PASM_TILE_PROLONG_SWEEP,      /* prolongation fused with the first post-smoothing
                                    sweep (float32 cycles)                            */
+  PASM_TILE_RESTRICT_FIRST,     /* coarse residual as R f - (R A) e (float32 cycles) */
   PASM_TILE_N
 };
 
@@ -132,14 +133,17 @@ typedef struct {
                           4, 8) of every sparse kernel on every level with at
                           least 16384 rows and keep the fastest; 0: fixed
                           default shapes [1]                                     */
-  double res_tol;      /* > 0: in pasm_solve and pasm_batch_solve a pair that
-                          meets the |dlambda| test is kept iterating while its
-                          relative residual
+  double res_tol;      /* > 0: a pair that meets the |dlambda| test is kept
+                          iterating while its relative residual
                           ||A u - lambda M u|| / (|lambda| ||u||_M) (the stopping
                           quantity of Section 5) exceeds res_tol, so a freeze on
                           a value that is not an eigenvalue is not reported as
-                          converged; checked with pasm_residuals on the steps
-                          where pairs freeze; 0: the |dlambda| test alone [0]   */
+                          converged.  Inside every step (pasm_step, the captured
+                          graph) for the state the step starts from, summed in
+                          float64 from the step's first outer residual; pasm_solve
+                          and pasm_batch_solve also check the state after the
+                          step with pasm_residuals on the steps where pairs
+                          freeze.  0: the |dlambda| test alone [0]               */
 } pasm_opts;
 
 typedef struct pasm_ctx pasm_ctx;
@@ -219,6 +223,9 @@ int pasm_project(pasm_ctx* ctx, const double* b, const double* c, double* bq, do
  * PASM_TILE_PROLONG_SWEEP, -1 means the autotuner timed the fused kernel
  * slower than its unfused pair (one sweep from zero + one sweep; residual +
  * restriction; prolongation + sweep) on this level, which then runs instead.
+ * PASM_TILE_RESTRICT_FIRST is above 0 only where the autotuner timed the
+ * restriction-first form of the coarse residual, R f - (R A) e with R A formed
+ * at setup, faster than both forms of R (f - A e); it then runs instead.
  * Errors: PASM_EINVAL. */
 int pasm_tiles(pasm_ctx* ctx, int level, int* chunks_per_thread);
 
@@ -234,7 +241,8 @@ int pasm_tile_rows(pasm_ctx* ctx, int level, int* rows_per_block);
 /* Set the tile shapes of `level` (a tuning cache: the values pasm_tiles and
  * pasm_tile_rows returned for a context of the same hierarchy, block width and
  * precision).  chunks_per_thread[PASM_TILE_N]: 0, 1, 2, 4 or 8, and -1 only for
- * PASM_TILE_JACOBI2_ZERO, PASM_TILE_RESID_RESTRICT and PASM_TILE_PROLONG_SWEEP;
+ * PASM_TILE_JACOBI2_ZERO, PASM_TILE_RESID_RESTRICT and PASM_TILE_PROLONG_SWEEP
+ * (PASM_TILE_RESTRICT_FIRST above 0 selects that form, mixed precision only);
  * rows_per_block[PASM_TILE_N] (NULL: all 0): 0, 1 or 4.  A shape that does not
  * fit the block width runs the default shape.  The autotuner of a later
  * pasm_init replaces them unless opts.autotune is 0 or the block width is the

@@ -28,7 +28,7 @@ PASM_INIT_COARSE, PASM_INIT_NESTED = 0, 1
 PASM_JACOBI, PASM_LEARNED, PASM_CG = 0, 1, 2
 PASM_PROJ_TENSOR, PASM_PROJ_FP64 = 0, 1
 TILE_KINDS = ("jacobi", "jacobi2_zero", "resid_restrict", "resid", "restrict", "prolong", "outer_rhs",
-              "outer_res", "border", "chain_r", "chain_p", "update", "prolong_sweep")
+              "outer_res", "border", "chain_r", "chain_p", "update", "prolong_sweep", "restrict_first")
 PASM_TILE_N = len(TILE_KINDS)
 NN_WEIGHTS = 2592
 

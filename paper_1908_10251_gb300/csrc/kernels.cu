@@ -442,6 +442,57 @@ void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, c
   L.bump();
 }
 
+// Restriction first: out (coarse) = R F - (R A) E, with R A formed once at setup.  The same
+// coarse residual as R (F - A E) in exact arithmetic; each coarse row gathers its fine rows of F and
+// the fine rows of E that R A couples to it (about 7 + 19 rows in 2D) instead of recomputing the
+// residual of every fine row it restricts (7 x 6 row loads).  Float32 cycles only.
+template <int CH>
+__global__ void __launch_bounds__(kBlock, (RowMinBlocks<float, CH>::v)) k_restrict_first(
+    int nc, const int* __restrict__ rrp, const int* __restrict__ rci, const float* __restrict__ rv,
+    const int* __restrict__ qrp, const int* __restrict__ qci, const float* __restrict__ qv,
+    const float* __restrict__ E, const float* __restrict__ F, float* __restrict__ out, int ldk, int tpr, int rpt) {
+  constexpr int V = 4;
+  const int rpb = kBlock / tpr;
+  const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+    const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
+    if (row >= nc) return;
+    float rf[CH][V], qe[CH][V];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < V; ++v) rf[c][v] = qe[c][v] = 0.f;
+    gather_rows<float, CH>(rci, rv, nullptr, 0.f, F, rrp[row], rrp[row + 1], lane, tpr, ldk, rf);
+    gather_rows<float, CH>(qci, qv, nullptr, 0.f, E, qrp[row], qrp[row + 1], lane, tpr, ldk, qe);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float o[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) o[v] = rf[c][v] - qe[c][v];
+      Vec16<float>::store(out + base + (c * tpr + lane) * V, o);
+    }
+  }
+}
+
+void restrict_first(const Launch& L, const DCsr& R, const DCsr& RA, const float* E, const float* F, float* out,
+                    int ldk) {
+  if (R.n_rows == 0) return;
+  Geo g = geometry<float>(ldk, L.geo);
+  const int rpb = kBlock / g.tpr;
+  const int rpt = rows_per_block<float>(L);
+  const int grid = (R.n_rows + rpb * rpt - 1) / (rpb * rpt);
+  {
+    const double nf = RA.n_cols, nc = R.n_rows;
+    L.rows(RA.n_cols);
+    L.begin(KC_RESID, (double)(R.nnz + RA.nnz) * 8.0 + 2.0 * (nc + 1) * 4.0 + 2.0 * nf * ldk * 4.0 + nc * ldk * 4.0,
+            2.0 * (double)(R.nnz + RA.nnz) * ldk + nc * ldk);
+  }
+  PASM_DISPATCH_CH(g.ch, k_restrict_first<CH><<<grid, kBlock, 0, L.s>>>(R.n_rows, R.rp, R.ci, R.v32, RA.rp, RA.ci,
+                                                                         RA.v32, E, F, out, ldk, g.tpr, rpt));
+  L.bump();
+}
+
 template void jacobi2_zero<float>(const Launch&, const DCsr&, const float*, float, const float*, float*, int);
 template void jacobi2_zero<double>(const Launch&, const DCsr&, const double*, double, const double*, double*, int);
 template void resid_restrict<float>(const Launch&, const DCsr&, const DCsr&, const float*, const float*, float*, int);

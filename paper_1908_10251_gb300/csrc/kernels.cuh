@@ -87,6 +87,10 @@ template <typename T>
 void jacobi2_zero(const Launch& L, const DCsr& A, const T* dinv, T omega, const T* F, T* out, int ldk);
 template <typename T>
 void resid_restrict(const Launch& L, const DCsr& R, const DCsr& A, const T* E, const T* F, T* out, int ldk);
+// out (coarse) = R F - RA E with RA = R A formed at setup (float32 cycles; same value as
+// resid_restrict in exact arithmetic)
+void restrict_first(const Launch& L, const DCsr& R, const DCsr& RA, const float* E, const float* F, float* out,
+                    int ldk);
 
 // Fd = lam .* (M U)  and  R = Fd - A U  (float64 arithmetic, R stored as TV)
 template <typename TV>
@@ -137,6 +141,11 @@ struct SecularArgs {
   int* steps;             // ldk in/out
   int* status;            // ldk out
   double tol;
+  // residual guard (null: none): rsum[i] = sum_j r_ji^2, rsum[ldk + i] = sum_j u_ji (lambda_i M u_i)_j
+  // of the state the step started from; a pair freezes only if sqrt(rsum[i] / (lambda_i rsum[ldk + i]))
+  // (the relative residual of Section 5) is at most res_tol
+  const double* rsum = nullptr;
+  double res_tol = 0.0;
   int score_norm;
   int window;             // half-width of the first root window
   int* diag;              // diagnostics: [0] = roots solved, [1] = full solves, [2] = iteration caps hit

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +58,7 @@ struct LevelDev {
   int n = 0;
   DCsr A, M;       // level stiffness and mass
   DCsr P, R;       // (l >= 1) P: level l-1 -> l, R = P^T
+  DCsr RA;         // (l >= 1, mixed precision) R A: the restriction-first residual of the float32 cycles
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   void* vF = nullptr;  // V-cycle right-hand side (precision of the cycle)
@@ -92,6 +94,7 @@ struct pasm_ctx {
   double* Uff = nullptr;  // mixed precision: U split into (hi, lo) float pairs for the gathers
   double *lam = nullptr, *lam2 = nullptr, *alpha = nullptr, *bz = nullptr, *bq = nullptr, *cq = nullptr,
          *g = nullptr, *uH = nullptr, *partials = nullptr;
+  double* rsum = nullptr;  // 2 x ldk: residual sums of the state a step starts from (opts.res_tol > 0)
   int *active = nullptr, *upd = nullptr, *steps = nullptr, *status = nullptr, *nact = nullptr, *diag = nullptr;
   int *active2 = nullptr, *steps2 = nullptr, *status2 = nullptr;
   int* h_nact = nullptr;  // pinned
@@ -210,6 +213,40 @@ int upload_csr(pasm_ctx* c, const pasm_csr& h, DCsr& d, bool shadow32, bool spli
     if (h.nnz) CK(cudaMemcpy(d.vff, f.data(), sizeof(float2) * (size_t)h.nnz, cudaMemcpyHostToDevice));
   }
   return PASM_OK;
+}
+
+// Host sparse product C = S B (CSR, columns ascending per row; row-by-row accumulation into a dense
+// marker row, Gustavson's method).  Values in float64, products summed in S's column order.
+void multiply_csr(const std::vector<int32_t>& srp, const std::vector<int32_t>& sci, const std::vector<double>& sv,
+                  int s_rows, const pasm_csr& b, std::vector<int32_t>& rp, std::vector<int32_t>& ci,
+                  std::vector<double>& v) {
+  rp.assign((size_t)s_rows + 1, 0);
+  ci.clear();
+  v.clear();
+  std::vector<int32_t> mark((size_t)b.n_cols, -1);
+  std::vector<double> acc((size_t)b.n_cols, 0.0);
+  std::vector<int32_t> cols;
+  for (int i = 0; i < s_rows; ++i) {
+    cols.clear();
+    for (int q = srp[(size_t)i]; q < srp[(size_t)i + 1]; ++q) {
+      const int j = sci[(size_t)q];
+      for (int64_t t = b.row_ptr[j]; t < b.row_ptr[j + 1]; ++t) {
+        const int col = b.col[t];
+        if (mark[(size_t)col] != i) {
+          mark[(size_t)col] = i;
+          acc[(size_t)col] = 0.0;
+          cols.push_back(col);
+        }
+        acc[(size_t)col] += sv[(size_t)q] * b.val[t];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int col : cols) {
+      ci.push_back(col);
+      v.push_back(acc[(size_t)col]);
+    }
+    rp[(size_t)i + 1] = (int32_t)ci.size();
+  }
 }
 
 // Host CSR transpose (R = P^T), columns ascending.
@@ -349,7 +386,15 @@ T* vcycle(pasm_ctx* c, int l, const TopOut* top = nullptr) {
     rowop<T>(launcher(c, l, PASM_TILE_JACOBI), OP_JACOBI, v.A, cur, F, cur, dinv<T>(v), om, tmp, ldk);
     std::swap(cur, tmp);
   }
-  if (fuse && c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] >= 0) {
+  bool restricted = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (fuse && v.RA.rp && c->geo[(size_t)l][PASM_TILE_RESTRICT_FIRST] > 0) {
+      restrict_first(launcher(c, l, PASM_TILE_RESTRICT_FIRST), v.R, v.RA, cur, F, (float*)c->lv[l - 1].vF, ldk);
+      restricted = true;
+    }
+  }
+  if (restricted) {
+  } else if (fuse && c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] >= 0) {
     resid_restrict<T>(launcher(c, l, PASM_TILE_RESID_RESTRICT), v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
   } else {
     rowop<T>(launcher(c, l, PASM_TILE_RESID), OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
@@ -401,6 +446,11 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
     // double-float outer residuals; X (the result u~) is left in (hi, lo) pairs
     if (!u_split) to_ff(L, (int64_t)v.n * c->ldk, U, c->Uff);
     outer_rhs_residual_ff(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, c->Uff, c->Fd, (float*)Ftop, c->ldk);
+    if (c->opts.res_tol > 0.0 && lt == c->nlev - 1) {  // the starting state's residual, for the freeze test
+      const int nb = residual_partials<float>(L, v.n, c->ldk, (const float*)Ftop, true, c->Fd, c->Uff, c->partials,
+                                              c->max_border_blocks);
+      column_sums(L, c->partials, nb, 2, c->ldk, c->rsum);
+    }
     // x = u + e reads u from its pair copy (in a step the state lives there alone)
     const TopOut first{c->Uff, true, X};
     T* e = vcycle<T>(c, lt, lt >= 1 ? &first : nullptr);
@@ -414,6 +464,10 @@ void bvp_impl(pasm_ctx* c, int lt, const double* lam, const double* U, double* X
     return;
   }
   outer_rhs_residual<T>(launcher(c, lt, PASM_TILE_OUTER_RHS), v.A, v.M, lam, U, c->Fd, Ftop, c->ldk);
+  if (c->opts.res_tol > 0.0 && lt == c->nlev - 1) {
+    const int nb = residual_partials<T>(L, v.n, c->ldk, Ftop, false, c->Fd, U, c->partials, c->max_border_blocks);
+    column_sums(L, c->partials, nb, 2, c->ldk, c->rsum);
+  }
   T* e = vcycle<T>(c, lt);
   outer_axpy<T>(L, v.n, U, e, X, c->ldk);
   for (int cyc = 1; cyc < c->opts.cycles_per_step; ++cyc) {
@@ -486,6 +540,10 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
   a.lam = ps.lam; a.alpha = c->alpha; a.g = c->g;
   a.active = ps.active; a.upd = c->upd; a.steps = ps.steps; a.status = ps.status;
   a.tol = ps.tol; a.score_norm = c->opts.score_norm; a.window = 3; a.diag = c->diag;
+  if (c->opts.res_tol > 0.0 && lt == c->nlev - 1) {
+    a.rsum = c->rsum;
+    a.res_tol = c->opts.res_tol;
+  }
   secular_select(L, a);
   if (c->proj_tc)
     proj_tc(L, c->projQ, c->g, nullptr, c->uH, nullptr, ldk, ldk, c->proj_hl, c->proj_tickets, c->proj_err,
@@ -568,6 +626,8 @@ int alloc_k(pasm_ctx* c, int k) {
     }
   }
   AL(K, &c->lam, ldk); AL(K, &c->lam2, ldk); AL(K, &c->alpha, ldk); AL(K, &c->bz, 2 * ldk);
+  AL(K, &c->rsum, 2 * ldk);
+  CK(cudaMemset(c->rsum, 0, sizeof(double) * 2 * ldk));  // zero sums pass the guard
   AL(K, &c->bq, nh); AL(K, &c->cq, nh); AL(K, &c->g, nh); AL(K, &c->uH, nh);
   AL(K, &c->partials, (size_t)c->max_border_blocks * 2 * ldk);
   AL(K, &c->active, ldk); AL(K, &c->upd, ldk); AL(K, &c->steps, ldk); AL(K, &c->status, ldk);
@@ -787,6 +847,14 @@ static int setup_impl(pasm_ctx* c, int n_levels, const pasm_csr* A, const pasm_c
       pasm_csr rt{p.n_cols, p.n_rows, p.nnz, rp.data(), ci.data(), rv.data()};
       r = upload_csr(c, rt, v.R, mixed, mixed);
       if (r) return r;
+      if (mixed) {
+        std::vector<int32_t> qrp, qci;
+        std::vector<double> qv;
+        multiply_csr(rp, ci, rv, p.n_cols, A[l], qrp, qci, qv);
+        pasm_csr ra{p.n_cols, A[l].n_cols, (int64_t)qci.size(), qrp.data(), qci.data(), qv.data()};
+        r = upload_csr(c, ra, v.RA, true, false);
+        if (r) return r;
+      }
     }
   }
   // coarse pencil: dense A_H, M_H -> Lambda_H, Q (Algorithm 2 step 1 on V_H)
@@ -869,7 +937,7 @@ int pasm_setup(pasm_ctx** out, int n_levels, const pasm_csr* A, const pasm_csr* 
       (o.init != PASM_INIT_COARSE && o.init != PASM_INIT_NESTED) ||
       (o.smoother != PASM_JACOBI && o.smoother != PASM_LEARNED && o.smoother != PASM_CG) ||
       (o.smoother == PASM_LEARNED && o.precision != PASM_MIXED) ||
-      (o.projection != PASM_PROJ_TENSOR && o.projection != PASM_PROJ_FP64))
+      (o.projection != PASM_PROJ_TENSOR && o.projection != PASM_PROJ_FP64) || !(o.res_tol >= 0.0))
     return PASM_EINVAL;
   int v = validate_levels(n_levels, A, M, P);
   if (v) return v;
@@ -974,6 +1042,14 @@ static int autotune(pasm_ctx* c) {
         rowop<float>(L, OP_SPMM, v.R, Tm, nullptr, nullptr, nullptr, om, (float*)w.vF, ldk);
       }, true);
       if (t_r + t_s < t_rr) c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] = -1;    // split: residual, then restriction
+      // restriction first (R f - (R A) e) against the faster of the two forms above
+      const float t_rf = pick(l, PASM_TILE_RESTRICT_FIRST, c32, [&](const Launch& L) {
+        restrict_first(L, v.R, v.RA, E, F, (float*)w.vF, ldk);
+      }, true);
+      if (!(t_rf < std::min(t_rr, t_r + t_s))) {
+        c->geo[(size_t)l][PASM_TILE_RESTRICT_FIRST] = 0;
+        c->rpt[(size_t)l][PASM_TILE_RESTRICT_FIRST] = 0;
+      }
       const float t_p = pick(l, PASM_TILE_PROLONG, c32, [&](const Launch& L) {
         rowop<float>(L, OP_SPMM_ADD, v.P, (float*)w.vE, E, nullptr, nullptr, om, E, ldk);
       }, true);
@@ -1324,6 +1400,7 @@ int pasm_set_tiles(pasm_ctx* c, int level, const int* chunks_per_thread, const i
   for (int q = 0; q < PASM_TILE_N; ++q) {
     const int ch = chunks_per_thread[q], r = rows_per_block ? rows_per_block[q] : 0;
     const bool fusable = q == PASM_TILE_JACOBI2_ZERO || q == PASM_TILE_RESID_RESTRICT || q == PASM_TILE_PROLONG_SWEEP;
+    if (q == PASM_TILE_RESTRICT_FIRST && ch > 0 && !c->lv[(size_t)level].RA.rp) return PASM_EINVAL;
     if (!(ch == 0 || ch == 1 || ch == 2 || ch == 4 || ch == 8 || (ch == -1 && fusable))) return PASM_EINVAL;
     if (!(r == 0 || r == 1 || r == 4)) return PASM_EINVAL;
   }

@@ -644,7 +644,9 @@ __global__ void __launch_bounds__(kSecThreads) k_secular(SecularArgs a) {
       a.alpha[i] = alpha;
       a.upd[i] = 1;
       const double rel = fabs(th - lam_prev) / fabs(th);
-      if (rel < a.tol) { a.active[i] = 0; a.status[i] = ST_CONVERGED; }
+      bool res_ok = true;
+      if (a.rsum) res_ok = sqrt(a.rsum[i]) <= a.res_tol * sqrt(fabs(lam_prev * a.rsum[a.ldk + i]));
+      if (rel < a.tol && res_ok) { a.active[i] = 0; a.status[i] = ST_CONVERGED; }
       else a.status[i] = ST_ACTIVE;
     }
   }

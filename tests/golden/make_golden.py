@@ -65,6 +65,9 @@ HISTORIES = {
     # no freezing (tol 0): shows which converged pairs are stable fixed points of the correction
     "cube_h128_H8_k32_nofreeze_history": (3, 128, 8, 32, 0.0, 40, False),
     "square_h1024_H16_k64_nofreeze_history": (2, 1024, 16, 64, 0.0, 40, False),
+    # h = 1/2048: the pairs of the clusters the vector check covers (0..41)
+    "square_h2048_H16_k42_history": (2, 2048, 16, 42, 1e-10, 40, False),
+    "square_h2048_H16_k42_nofreeze_history": (2, 2048, 16, 42, 0.0, 40, False),
 }
 
 

@@ -42,7 +42,10 @@ def test_autotuned_tiles_match_default(pg, precision):
         pg.pasm_init(ctx, 32, 1e-12)
         tiles = pg.pasm_tiles(ctx, len(H.levels) - 1)
         assert all(v in (-1, 0, 1, 2, 4, 8) for v in tiles.values())
+        assert tiles["restrict_first"] >= 0
         assert all(v >= 0 for kk, v in tiles.items() if kk not in ("jacobi2_zero", "resid_restrict", "prolong_sweep"))
+        if precision == 0:
+            assert tiles["restrict_first"] == 0
         rows = pg.pasm_tile_rows(ctx, len(H.levels) - 1)
         assert all(v in (0, 1, 4) for v in rows.values())
         if tune and precision == 1:
@@ -108,3 +111,37 @@ def test_saved_tiles_reproduce_the_tuned_run(pg):
             with pytest.raises(RuntimeError):
                 pg.pasm_set_tiles(ctx, len(H.levels) - 1, saved[len(H.levels) - 1][0], {"jacobi": 2})
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
+@pytest.mark.parametrize("form", ["fused", "split", "restrict_first"])
+def test_coarse_residual_forms_match_the_oracle_cycle(pg, form):
+    """The three forms of the float32 coarse residual -- R (f - A e) with the
+    fine residual recomputed per coarse row, the residual then the
+    restriction, and R f - (R A) e with R A formed at setup -- set on every
+    level through pasm_set_tiles, each give the oracle's two V-cycles of
+    Algorithm 1 step 1 to float32 accuracy."""
+    import oracle
+    from oracle import pasm as op
+    H = mg.build_hierarchy(2, 64, 8)
+    opts = pg.pasm_default_opts(precision=1, autotune=0)
+    ctx = pg.pasm_setup([lv.A for lv in H.levels], [lv.M for lv in H.levels], H.P, opts,
+                        torch.cuda.current_stream().cuda_stream)
+    for lv in range(1, len(H.levels)):
+        ch = {"resid_restrict": -1 if form == "split" else 0,
+              "restrict_first": 2 if form == "restrict_first" else 0}
+        rows = {"restrict_first": 4} if form == "restrict_first" else {}
+        pg.pasm_set_tiles(ctx, lv, ch, rows)
+    prob = oracle.Problem.from_hierarchy(H)
+    k = 6
+    lam, U = oracle.initial_state(prob, k)
+    pg.pasm_init(ctx, k, 0.0, lam, U)
+    Uh = np.zeros_like(U)
+    pg.pasm_bvp(ctx, lam, U, Uh)
+    Uo = op.bvp_solve(prob, lam, U)
+    err = max(np.abs(Uh[:, j] - Uo[:, j]).max() / np.abs(Uo[:, j]).max() for j in range(k))
+    assert err < 1e-5, err
+    # float64 contexts have no R A: the form is refused there
+    ctx64 = pg.pasm_setup([lv.A for lv in H.levels], [lv.M for lv in H.levels], H.P,
+                          pg.pasm_default_opts(precision=0, autotune=0), torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(RuntimeError):
+        pg.pasm_set_tiles(ctx64, len(H.levels) - 1, {"restrict_first": 2})

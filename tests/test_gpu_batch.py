@@ -160,3 +160,38 @@ def test_residual_guard_rejects_spurious_freezes(pg):
     conv = status == 1
     assert np.all(res[conv] <= 1e-3 * (1 + 1e-6)), res[conv]
     assert (code == 5) == bool(np.any(~conv))
+
+
+def test_residual_guard_inside_the_step(pg):
+    """The same problem driven by pasm_step alone (no host-side check): with
+    opts.res_tol = 1e-3 the step itself freezes a pair only when the state it
+    started from has relative residual <= 1e-3, so every pair reported
+    converged after 40 steps has a small residual (recomputed in float64 on the
+    CPU; the freezing step's own correction can only improve it, factor 2 of
+    slack), while without the guard some converged pairs have residuals near 4."""
+    N, k = 512, 16
+    H = mg.build_hierarchy(2, N, 16, kappa=mg.gaussian_log_field(N, 1001))
+    A, M, P = parts(H)
+
+    def run(res_tol):
+        opts = pg.pasm_default_opts(precision=1, res_tol=res_tol)
+        ctx = pg.pasm_setup(A, M, P, opts, torch.cuda.current_stream().cuda_stream)
+        pg.pasm_init(ctx, k, 1e-10)
+        for _ in range(40):
+            pg.pasm_step(ctx)
+        lam = np.zeros(k)
+        U = np.zeros((H.fine.n, k))
+        steps = np.zeros(k, dtype=np.int32)
+        status = np.zeros(k, dtype=np.int32)
+        pg.pasm_get(ctx, lam, U, steps, status)
+        pg.pasm_destroy(ctx)
+        MU = H.fine.M @ U
+        res = np.linalg.norm(H.fine.A @ U - MU * lam[None, :], axis=0) / (lam * np.sqrt(np.einsum("ij,ij->j", U, MU)))
+        return status, res
+
+    status0, res0 = run(0.0)
+    assert np.any((status0 == 1) & (res0 > 1e-3))
+    status, res = run(1e-3)
+    conv = status == 1
+    assert conv.any()
+    assert np.all(res[conv] <= 2e-3), res[conv]
