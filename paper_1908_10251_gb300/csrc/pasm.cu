@@ -393,10 +393,9 @@ T* vcycle(pasm_ctx* c, int l, const TopOut* top = nullptr) {
       restricted = true;
     }
   }
-  if (restricted) {
-  } else if (fuse && c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] >= 0) {
+  if (!restricted && fuse && c->geo[(size_t)l][PASM_TILE_RESID_RESTRICT] >= 0) {
     resid_restrict<T>(launcher(c, l, PASM_TILE_RESID_RESTRICT), v.R, v.A, cur, F, (T*)c->lv[l - 1].vF, ldk);
-  } else {
+  } else if (!restricted) {
     rowop<T>(launcher(c, l, PASM_TILE_RESID), OP_RESID, v.A, cur, F, nullptr, nullptr, om, tmp, ldk);
     rowop<T>(launcher(c, l, PASM_TILE_RESTRICT), OP_SPMM, v.R, tmp, nullptr, nullptr, nullptr, om,
              (T*)c->lv[l - 1].vF, ldk);
