@@ -924,11 +924,12 @@ template <int CH, bool BFF>
 __global__ void __launch_bounds__(kBlock)
     k_jacobi_axpy_ff(int n, const int* __restrict__ rp, const int* __restrict__ ci, const float* __restrict__ av,
                      const float* __restrict__ E, const float* __restrict__ F, const float* __restrict__ dinv,
-                     float omega, const double* B, double* X, int ldk, int tpr) {
+                     float omega, const double* B, double* X, int ldk, int tpr, int rpt) {
   constexpr int V = 4;
   const int rpb = kBlock / tpr;
-  const int row = blockIdx.x * rpb + threadIdx.x / tpr;
   const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+  const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
   if (row >= n) return;
   float acc[CH][V];
 #pragma unroll
@@ -966,6 +967,7 @@ __global__ void __launch_bounds__(kBlock)
     *reinterpret_cast<float4*>(X + off) = make_float4(h[0], l[0], h[1], l[1]);
     *reinterpret_cast<float4*>(X + off + 2) = make_float4(h[2], l[2], h[3], l[3]);
   }
+  }
 }
 
 void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float* F, const float* dinv, float omega,
@@ -973,7 +975,8 @@ void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float*
   if (A.n_rows == 0) return;
   const Geo g = geometry<float>(ldk, L.geo);
   const int rpb = kBlock / g.tpr;
-  const int grid = (A.n_rows + rpb - 1) / rpb;
+  const int rpt = rows_per_block<float>(L);  // the plain sweep's choice on this level
+  const int grid = (A.n_rows + rpb * rpt - 1) / (rpb * rpt);
   {
     const double rows = A.n_rows, cols = A.n_cols, nnz = (double)A.nnz;
     L.rows(A.n_rows);
@@ -982,10 +985,10 @@ void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float*
   }
   if (b_ff) {
     PASM_DISPATCH_CH(g.ch, k_jacobi_axpy_ff<CH, true><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v32, E, F, dinv,
-                                                                                 omega, B, X, ldk, g.tpr));
+                                                                                 omega, B, X, ldk, g.tpr, rpt));
   } else {
     PASM_DISPATCH_CH(g.ch, k_jacobi_axpy_ff<CH, false><<<grid, kBlock, 0, L.s>>>(A.n_rows, A.rp, A.ci, A.v32, E, F,
-                                                                                  dinv, omega, B, X, ldk, g.tpr));
+                                                                                  dinv, omega, B, X, ldk, g.tpr, rpt));
   }
   L.bump();
 }
