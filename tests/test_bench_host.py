@@ -28,12 +28,16 @@ def test_clusters_and_first_reach():
 
 
 def test_first_reach_with_a_shorter_reference_table():
-    """More pairs than reference eigenvalues (the h = 1/2048, k = 128 workload
-    has a 48-value table): pairs past the table never count, the rest do."""
+    """More pairs than reference eigenvalues or than the oracle's history
+    covers (the h = 1/2048, k = 128 workload: 136 reference values, oracle
+    histories of pairs 0..41): pairs past the table never count, the rest do;
+    the reference set is the oracle's stable pairs among 0..41, without pair
+    11 (reached, then left: an unstable fixed point)."""
     ref = np.array([1.0, 2.0, 3.0])
     hist = np.array([[1.0, 2.0, 3.0, 4.0, 5.0]])
     assert list(bench.first_reach(hist, ref, 1e-9, ref)) == [0, 0, 0, -1, -1]
-    assert bench.reference_set(bench.WORK_H2048) is None
+    rs = bench.reference_set(bench.WORK_H2048)
+    assert rs.max() < 42 and list(rs[:3]) == [0, 1, 2] and 11 not in rs
     conv, S = bench.time_to_target(np.array([0, 3, -1, -1]), None, 60)
     assert (conv, S) == (2, 3)
 
