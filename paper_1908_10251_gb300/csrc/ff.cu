@@ -331,6 +331,86 @@ __global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm_ff(int n, con
   }
 }
 
+// outA = S XA and outM = S XM together (the two restriction chains of the bordering products): one
+// load of S's indices and values serves both; each product sees the same terms in the same order
+// as two separate k_spmm_ff launches.
+template <int CH, int N, bool FFIN, bool EX>
+__device__ __forceinline__ void gather_group_ff2(const int* __restrict__ ci, const float2* __restrict__ av,
+                                                 const double* __restrict__ XA, const double* __restrict__ XM,
+                                                 int p, int lane, int tpr, int ldk, float (&ah)[CH][2],
+                                                 float (&al)[CH][2], float (&mh)[CH][2], float (&ml)[CH][2]) {
+  int j[N];
+  float2 a[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    j[u] = __ldg(ci + p + u);
+    a[u] = __ldg(av + p + u);
+  }
+  float xh[N][CH][2], xl[N][CH][2], yh[N][CH][2], yl[N][CH][2];
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const size_t off = (size_t)j[u] * ldk + (c * tpr + lane) * 2;
+      load_pair<FFIN>(XA, off, xh[u][c], xl[u][c]);
+      load_pair<FFIN>(XM, off, yh[u][c], yl[u][c]);
+    }
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        if (EX) {
+          ff_mac_exact(ah[c][v], al[c][v], a[u].x, xh[u][c][v], xl[u][c][v]);
+          ff_mac_exact(mh[c][v], ml[c][v], a[u].x, yh[u][c][v], yl[u][c][v]);
+        } else {
+          ff_mac(ah[c][v], al[c][v], a[u].x, a[u].y, xh[u][c][v], xl[u][c][v]);
+          ff_mac(mh[c][v], ml[c][v], a[u].x, a[u].y, yh[u][c][v], yl[u][c][v]);
+        }
+      }
+}
+
+template <int CH, bool FFIN, bool FFOUT, bool EX>
+__global__ void __launch_bounds__(kBlock, kMinBlocksGather) k_spmm2_ff(int n, const int* __restrict__ rp,
+                                                                     const int* __restrict__ ci,
+                                                                     const float2* __restrict__ av,
+                                                                     const double* __restrict__ XA,
+                                                                     const double* __restrict__ XM,
+                                                                     double* __restrict__ outA,
+                                                                     double* __restrict__ outM, int ldk, int tpr,
+                                                                     int rpt) {
+  const int rpb = kBlock / tpr;
+  const int lane = threadIdx.x % tpr;
+  for (int rr = 0; rr < rpt; ++rr) {
+    const int row = (blockIdx.x * rpt + rr) * rpb + threadIdx.x / tpr;
+    if (row >= n) return;
+    float ah[CH][2], al[CH][2], mh[CH][2], ml[CH][2];
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int v = 0; v < 2; ++v) ah[c][v] = al[c][v] = mh[c][v] = ml[c][v] = 0.f;
+    int p = __ldg(rp + row);
+    const int p1 = __ldg(rp + row + 1);
+    for (; p + 4 <= p1; p += 4) gather_group_ff2<CH, 4, FFIN, EX>(ci, av, XA, XM, p, lane, tpr, ldk, ah, al, mh, ml);
+    const int rem = p1 - p;
+    if (rem == 3) gather_group_ff2<CH, 3, FFIN, EX>(ci, av, XA, XM, p, lane, tpr, ldk, ah, al, mh, ml);
+    else if (rem == 2) gather_group_ff2<CH, 2, FFIN, EX>(ci, av, XA, XM, p, lane, tpr, ldk, ah, al, mh, ml);
+    else if (rem == 1) gather_group_ff2<CH, 1, FFIN, EX>(ci, av, XA, XM, p, lane, tpr, ldk, ah, al, mh, ml);
+    const size_t base = (size_t)row * ldk;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        ff_norm(ah[c][v], al[c][v]);
+        ff_norm(mh[c][v], ml[c][v]);
+      }
+      store_pair<FFOUT>(outA, base + (c * tpr + lane) * 2, ah[c], al[c]);
+      store_pair<FFOUT>(outM, base + (c * tpr + lane) * 2, mh[c], ml[c]);
+    }
+  }
+}
+
 // X = B + E with E float32, X as float pairs; B as float pairs (may alias X)
 // or float64.
 template <bool BFF>
@@ -533,6 +613,33 @@ void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double*
   else if (out_ff) { PASM_FF_SPMM(false, true); }
   else { PASM_FF_SPMM(false, false); }
 #undef PASM_FF_SPMM
+  L.bump();
+}
+
+void spmm2_ff(const Launch& L, const DCsr& S, const double* XA, const double* XM, bool x_ff, double* outA,
+              double* outM, bool out_ff, int ldk) {
+  if (S.n_rows == 0) return;
+  const Geo g = geometry_ff(ldk, L.geo);
+  const int rpb = kBlock / g.tpr, rpt = ff_rows(L);
+  const int grid = (S.n_rows + rpb * rpt - 1) / (rpb * rpt);
+  {
+    const double rows = S.n_rows, cols = S.n_cols, nnz = (double)S.nnz;
+    L.rows(S.n_rows);
+    L.begin(KC_SPMM, nnz * 12.0 + (rows + 1) * 4.0 + 2.0 * (cols + rows) * ldk * 8.0, 4.0 * nnz * ldk);
+  }
+#define PASM_FF_SPMM2(FI, FO)                                                                                    \
+  if (S.exact32) {                                                                                               \
+    PASM_FF_DISPATCH(g.ch, k_spmm2_ff<CH, FI, FO, true><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, XA,  \
+                                                                                   XM, outA, outM, ldk, g.tpr, rpt)); \
+  } else {                                                                                                       \
+    PASM_FF_DISPATCH(g.ch, k_spmm2_ff<CH, FI, FO, false><<<grid, kBlock, 0, L.s>>>(S.n_rows, S.rp, S.ci, S.vff, XA, \
+                                                                                    XM, outA, outM, ldk, g.tpr, rpt)); \
+  }
+  if (x_ff && out_ff) { PASM_FF_SPMM2(true, true); }
+  else if (x_ff) { PASM_FF_SPMM2(true, false); }
+  else if (out_ff) { PASM_FF_SPMM2(false, true); }
+  else { PASM_FF_SPMM2(false, false); }
+#undef PASM_FF_SPMM2
   L.bump();
 }
 

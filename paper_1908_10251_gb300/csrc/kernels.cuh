@@ -193,6 +193,9 @@ void jacobi_axpy_ff(const Launch& L, const DCsr& A, const float* E, const float*
                     const double* B, bool b_ff, double* X, int ldk);
 // out = S X; x_ff / out_ff: X / out in pairs (else float64).
 void spmm_ff(const Launch& L, const DCsr& S, const double* X, bool x_ff, double* out, bool out_ff, int ldk);
+// outA = S XA, outM = S XM in one launch (each as spmm_ff computes it)
+void spmm2_ff(const Launch& L, const DCsr& S, const double* XA, const double* XM, bool x_ff, double* outA,
+              double* outM, bool out_ff, int ldk);
 // X = B + E (X in pairs; B in pairs if b_ff, else float64; X may alias B).
 void axpy_ff(const Launch& L, int n, const double* B, bool b_ff, const float* E, double* X, int ldk);
 // Conversions of total entries: float64 -> pairs (may be in place), pairs -> float64.

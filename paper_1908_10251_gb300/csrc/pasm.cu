@@ -521,8 +521,7 @@ void augmented(pasm_ctx* c, int lt, const double* X, const PairState& ps) {
     if (ff) {
       // pairs down to level 1, float64 on the coarse level for the projection
       const Launch Lr = launcher(c, l, PASM_TILE_CHAIN_R);
-      spmm_ff(Lr, c->lv[l].R, sa, true, c->lv[l - 1].BA, l - 1 >= 1, ldk);
-      spmm_ff(Lr, c->lv[l].R, sm, true, c->lv[l - 1].BM, l - 1 >= 1, ldk);
+      spmm2_ff(Lr, c->lv[l].R, sa, sm, true, c->lv[l - 1].BA, c->lv[l - 1].BM, l - 1 >= 1, ldk);
     } else {
       const Launch Lr = launcher(c, l, PASM_TILE_CHAIN_R);
       rowop<double>(Lr, OP_SPMM, c->lv[l].R, sa, nullptr, nullptr, nullptr, 0.0, c->lv[l - 1].BA, ldk);
@@ -1064,8 +1063,9 @@ static int autotune(pasm_ctx* c) {
       pick(l, PASM_TILE_BORDER, c64, [&](const Launch& L) {
         border_products_ff(L, v.A, v.M, c->X, c->YA, c->YM, c->partials, ldk, c->max_border_blocks);
       });
-      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) { spmm_ff(L, v.R, c->YA, true, w.BA, l - 1 >= 1, ldk); },
-           true);
+      pick(l, PASM_TILE_CHAIN_R, c64, [&](const Launch& L) {
+        spmm2_ff(L, v.R, c->YA, c->YM, true, w.BA, w.BM, l - 1 >= 1, ldk);
+      }, true);
       if (l < c->nlev - 1)
         pick(l, PASM_TILE_CHAIN_P, c64, [&](const Launch& L) { spmm_ff(L, v.P, w.BA, l - 1 >= 1, v.BA, true, ldk); },
              true);
